@@ -1,0 +1,447 @@
+"""FP64 CPU oracle for the RMHMC hot path — TEST INFRASTRUCTURE ONLY.
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline legs of
+`bench.py` may import this package.  It shares no code with the CUDA library
+(`paper_2112_04556_gb300`); the two meet only through the seeded inputs of
+`paper_2112_04556_gb300.inputs`, which hold none of the method's arithmetic.
+
+The per-site primitives (Laplacian, its link derivative, gauge loops, the
+exponential, Philox) are plain C in `oracle.c`; the algorithms built on them
+(CG, Chebyshev moments and windows, rational mass term, kinetic force,
+implicit leapfrog, Metropolis) are written below in numpy, step by step in the
+order the method states them.  Everything is float64.
+
+Paper: Nguyen, Boyle, Christ, Jang, Jung, "Riemannian manifold hybrid Monte
+Carlo in lattice QCD", LATTICE2021 (arXiv:2112.04556).
+  Sec. 2, Eq. (3): adjoint covariant Laplacian, normalised -Delta_G/16.
+  Sec. 2, Eq. (4): per-mode power spectrum <F|B(lambda)|F> / Tr B(lambda),
+                   B(lambda) = sum_i c_i T_i[-Delta_G/16].
+  Sec. 3, Eq. (5): H = 1/2 Tr P^dag M^{-1} P + S[U] (+ log|M|, not evaluated).
+  Sec. 3, Eq. (6): M = [c + rational function of -Delta_G/16]^{-2}.
+  Sec. 3: implicit (generalised) leapfrog of Girolami & Calderhead.
+
+Parity pins: every function here is checked in tests/test_oracle_*.py against
+closed forms, invariants, dense linear algebra or finite differences; the one
+exception is stated in `leapfrog_step` (exact volume preservation of the
+group-valued implicit step: parity unpinned).
+"""
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force=False):
+    """Compile oracle.c into liboracle.so (gcc, -O2, OpenMP over sites)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        return _SO
+    tmp = _SO + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fopenmp", "-fPIC", "-shared",
+                           src, "-o", tmp, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        P = ctypes.c_void_p
+        I4 = ctypes.POINTER(ctypes.c_int)
+        d = ctypes.c_double
+        L.orc_lap.argtypes = [I4, P, P, P, ctypes.c_int]
+        L.orc_lap_link_grad.argtypes = [I4, P, P, P, ctypes.c_int, P, P]
+        L.orc_action_density.argtypes = [I4, P, d, d, P, P]
+        L.orc_gauge_force.argtypes = [I4, P, d, d, P]
+        L.orc_link_update.argtypes = [I4, P, d, P, P]
+        L.orc_exp_i.argtypes = [ctypes.c_long, P, P]
+        L.orc_mat_mul.argtypes = [ctypes.c_long, P, P, P]
+        L.orc_coef_to_mat.argtypes = [ctypes.c_long, P, P]
+        L.orc_mat_to_coef.argtypes = [ctypes.c_long, P, P]
+        L.orc_philox4x32_10.argtypes = [P, P, P]
+        L.orc_gauss_field.argtypes = [I4, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, P]
+        L.orc_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
+        L.orc_uniform.restype = d
+        L.orc_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _dims(L):
+    return (ctypes.c_int * 4)(*[int(v) for v in L])
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def num_threads():
+    return lib().orc_num_threads()
+
+
+def volume(L):
+    return int(np.prod(L))
+
+
+# --------------------------------------------------------------------------
+# Sec. 2, Eq. (3): A = -Delta_G/16 and its link derivative
+# --------------------------------------------------------------------------
+
+def lap(L, U, X):
+    """A X with A = -Delta_G/16 (Eq. 3), X of shape [V,4,8] or [n,V,4,8]."""
+    U = _c(U, np.complex128)
+    X = _c(X, np.float64)
+    single = X.ndim == 3
+    Xs = X[None] if single else X
+    Y = np.empty_like(Xs)
+    lib().orc_lap(_dims(L), _p(U), _p(Xs), _p(Y), Xs.shape[0])
+    return Y[0] if single else Y
+
+
+def lap_link_grad(L, U, X, Z, w):
+    """G^a(y,nu) = sum_f w_f d<Z_f, A X_f>/dw^a for U_nu(y) -> exp(i w^a T^a) U_nu(y)."""
+    U = _c(U, np.complex128)
+    X = _c(X, np.float64)
+    Z = _c(Z, np.float64)
+    if X.ndim == 3:
+        X, Z = X[None], Z[None]
+    w = _c(np.atleast_1d(w), np.float64)
+    G = np.empty(X.shape[1:], dtype=np.float64)
+    lib().orc_lap_link_grad(_dims(L), _p(U), _p(X), _p(Z), X.shape[0], _p(w), _p(G))
+    return G
+
+
+def inner(X, Y):
+    """<X,Y> = sum_{x,mu,a} X^a Y^a (= 2 sum Tr XY)."""
+    return float(np.dot(np.ravel(X), np.ravel(Y)))
+
+
+# --------------------------------------------------------------------------
+# gauge action and force (Sec. 2: F_G = -dS/dU with left multiplication)
+# --------------------------------------------------------------------------
+
+def action_density(L, U, beta, c1=0.0):
+    U = _c(U, np.complex128)
+    V = volume(L)
+    s = np.empty(V)
+    p = np.empty(V)
+    lib().orc_action_density(_dims(L), _p(U), float(beta), float(c1), _p(s), _p(p))
+    return s, p
+
+
+def action(L, U, beta, c1=0.0):
+    """S = beta sum [c0 sum_plaq (1 - ReTr/3) + c1 sum_rect (1 - ReTr/3)], c0 = 1 - 8 c1;
+    returns (S, plaquette average), both summed exactly (math.fsum)."""
+    s, p = action_density(L, U, beta, c1)
+    return math.fsum(s), math.fsum(p) / len(p)
+
+
+def gauge_force(L, U, beta, c1=0.0):
+    """F^a_mu(x) = -dS/dw^a, U_mu(x) -> exp(i w^a T^a) U_mu(x); shape [V,4,8]."""
+    U = _c(U, np.complex128)
+    F = np.empty((volume(L), 4, 8))
+    lib().orc_gauge_force(_dims(L), _p(U), float(beta), float(c1), _p(F))
+    return F
+
+
+def link_update(L, U, V, eps):
+    """U <- exp(i eps V) U per link (Taylor series with scaling and squaring)."""
+    U = _c(U, np.complex128)
+    V = _c(V, np.float64)
+    out = np.empty_like(U)
+    lib().orc_link_update(_dims(L), _p(V), float(eps), _p(U), _p(out))
+    return out
+
+
+def exp_i(h):
+    """exp(i sum_a h^a T^a) for h of shape [..., 8]."""
+    h = _c(h, np.float64)
+    n = h.size // 8
+    out = np.empty(h.shape[:-1] + (3, 3), dtype=np.complex128)
+    lib().orc_exp_i(n, _p(h), _p(out))
+    return out
+
+
+def coef_to_mat(p):
+    p = _c(p, np.float64)
+    out = np.empty(p.shape[:-1] + (3, 3), dtype=np.complex128)
+    lib().orc_coef_to_mat(p.size // 8, _p(p), _p(out))
+    return out
+
+
+def mat_to_coef(m):
+    m = _c(m, np.complex128)
+    out = np.empty(m.shape[:-2] + (8,))
+    lib().orc_mat_to_coef(m.size // 9, _p(m), _p(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# counter-based random numbers (Philox4x32-10, Salmon et al. SC'11)
+# --------------------------------------------------------------------------
+
+def philox4x32_10(ctr, key):
+    c = _c(np.asarray(ctr, dtype=np.uint32), np.uint32)
+    k = _c(np.asarray(key, dtype=np.uint32), np.uint32)
+    out = np.empty(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def gauss_field(L, seed, stream, tag=0):
+    """Gaussian su(3) field [V,4,8] from Philox block (n/2, site, stream, tag), key = seed."""
+    out = np.empty((volume(L), 4, 8))
+    lib().orc_gauss_field(_dims(L), int(seed), int(stream), int(tag), _p(out))
+    return out
+
+
+def uniform(seed, stream, tag=1):
+    return lib().orc_uniform(int(seed), int(stream), int(tag))
+
+
+# --------------------------------------------------------------------------
+# Krylov solves: plain CG, one shift at a time (definition of (A+sigma)^{-1} b)
+# --------------------------------------------------------------------------
+
+def cg(apply, b, tol=1e-13, maxiter=10000):
+    """Textbook conjugate gradients for a symmetric positive definite operator.
+    Stops when the true relative residual |b - A x| / |b| <= tol."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = inner(r, r)
+    bb = inner(b, b)
+    if bb == 0.0:
+        return x, 0, 0.0
+    it = 0
+    while it < maxiter:
+        q = apply(p)
+        alpha = rr / inner(p, q)
+        x += alpha * p
+        r -= alpha * q
+        rr_new = inner(r, r)
+        it += 1
+        if math.sqrt(rr_new / bb) <= 0.5 * tol:
+            true_r = b - apply(x)
+            res = math.sqrt(inner(true_r, true_r) / bb)
+            if res <= tol:
+                return x, it, res
+            r = true_r
+            rr_new = inner(r, r)
+            p = r.copy()
+            rr = rr_new
+            continue
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    true_r = b - apply(x)
+    raise RuntimeError("oracle CG did not converge: residual %g" % math.sqrt(inner(true_r, true_r) / bb))
+
+
+def shifted_solves(L, U, b, sigma, tol=1e-13):
+    """x_j = (A + sigma_j)^{-1} b for every shift, each by its own CG."""
+    xs = []
+    for s in sigma:
+        x, _, _ = cg(lambda v, s=s: lap(L, U, v) + s * v, b, tol)
+        xs.append(x)
+    return np.array(xs)
+
+
+def rational_apply(L, U, b, mass, tol=1e-13):
+    """R(A) b = c b + sum_j alpha_j (A + sigma_j)^{-1} b (Eq. 6 in partial fractions).
+    Returns (R b, [x_j])."""
+    xs = shifted_solves(L, U, b, mass["sigma"], tol)
+    y = mass["c"] * b
+    for a, x in zip(mass["alpha"], xs):
+        y = y + a * x
+    return y, xs
+
+
+# --------------------------------------------------------------------------
+# Sec. 2, Eq. (4): Chebyshev band-pass filters and the per-mode spectrum
+# --------------------------------------------------------------------------
+
+def cheb_moments(L, U, F, N):
+    """mu_k = <F, T_k(2A - 1) F>, k = 0..N, by the plain three-term recurrence
+    v_0 = F, v_1 = (2A-1) F, v_{k+1} = 2 (2A-1) v_k - v_{k-1}."""
+    H = lambda v: 2.0 * lap(L, U, v) - v
+    mu = np.zeros(N + 1)
+    v_prev = F
+    mu[0] = inner(F, F)
+    if N == 0:
+        return mu
+    v = H(F)
+    mu[1] = inner(F, v)
+    for k in range(2, N + 1):
+        v_prev, v = v, 2.0 * H(v) - v_prev
+        mu[k] = inner(F, v)
+    return mu
+
+
+def jackson(N):
+    """Jackson damping g_k, k = 0..N (kernel polynomial method)."""
+    k = np.arange(N + 1)
+    q = math.pi / (N + 1)
+    return ((N - k + 1) * np.cos(q * k) + np.sin(q * k) / math.tan(q)) / (N + 1)
+
+
+def window_coeffs(edges, N, kernel="jackson"):
+    """C[w,k]: Chebyshev coefficients (in x = 2 lambda - 1) of the indicator of the
+    window [edges[w], edges[w+1]] of eigenvalues of A, times the damping g_k."""
+    edges = np.asarray(edges, dtype=np.float64)
+    theta = np.arccos(np.clip(2.0 * edges - 1.0, -1.0, 1.0))
+    k = np.arange(1, N + 1)
+    C = np.zeros((len(edges) - 1, N + 1))
+    for w in range(len(edges) - 1):
+        ta, tb = theta[w], theta[w + 1]
+        C[w, 0] = (ta - tb) / math.pi
+        C[w, 1:] = 2.0 * (np.sin(k * ta) - np.sin(k * tb)) / (k * math.pi)
+    if kernel == "jackson":
+        C *= jackson(N)[None, :]
+    return C
+
+
+def power_spectrum(L, U, forces, noises, N, edges, kernel="jackson"):
+    """Eq. (4): spec[f,w] = <F_f|B_w|F_f> / Tr B_w, with B_w = sum_k C[w,k] T_k(2A-1) and
+    Tr B_w over the full [V,4,8] space estimated as the mean of <eta|B_w|eta> over the
+    supplied noise fields (Hutchinson).  Returns (spec, num, tr, moments)."""
+    C = window_coeffs(edges, N, kernel)
+    mf = np.array([cheb_moments(L, U, F, N) for F in forces])
+    mn = np.array([cheb_moments(L, U, e, N) for e in noises])
+    num = mf @ C.T
+    tr = (mn @ C.T).mean(axis=0)
+    return num / tr[None, :], num, tr, np.concatenate([mf, mn])
+
+
+# --------------------------------------------------------------------------
+# Sec. 3, Eqs. (5)-(6): mass term, kinetic energy and force
+# --------------------------------------------------------------------------
+
+def identity_mass():
+    return {"c": 1.0, "alpha": np.zeros(0), "sigma": np.zeros(0), "kappa": 0.0}
+
+
+def kinetic(L, U, P, mass, tol=1e-13):
+    """T = 1/2 <P, M^{-1} P> with M = R(A)^{-2}: T = 1/2 |R P|^2.
+    Also the velocity V = M^{-1} P = R(R P) and the kinetic force
+    F_K = -dT/dw = sum_j alpha_j <Z_j, (dA/dw) X_j>,
+    X_j = (A+sigma_j)^{-1} P, Z_j = (A+sigma_j)^{-1} R P."""
+    Y, X = rational_apply(L, U, P, mass, tol)
+    Vel, Z = rational_apply(L, U, Y, mass, tol)
+    T = 0.5 * math.fsum((Y * Y).ravel())
+    if len(mass["sigma"]):
+        FK = lap_link_grad(L, U, X, Z, mass["alpha"])
+    else:
+        FK = np.zeros_like(P)
+    return T, FK, Vel
+
+
+def heatbath(L, U, xi, mass, tol=1e-13):
+    """Momentum refresh P = M^{1/2} xi, taken as m(A) R(A) xi with m(A) = (1-kappa) + kappa A
+    (R ~ m^{-1/2}, so m R ~ m^{1/2} = M^{1/2} to the accuracy of the rational fit)."""
+    y, _ = rational_apply(L, U, xi, mass, tol)
+    k = mass.get("kappa", 0.0)
+    return (1.0 - k) * y + k * lap(L, U, y)
+
+
+def hamiltonian(L, U, P, beta, c1, mass, tol=1e-13):
+    """H = 1/2 <P, M^{-1} P> + S[U] (Eq. 5 without the log|M| term)."""
+    T, _, _ = kinetic(L, U, P, mass, tol)
+    S, plaq = action(L, U, beta, c1)
+    return T + S, T, S, plaq
+
+
+def _maxabs(a):
+    return float(np.max(np.abs(a))) if a.size else 0.0
+
+
+def leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol=1e-13, fp_tol=1e-13, fp_maxit=100):
+    """One generalised-leapfrog step (Sec. 3; Girolami & Calderhead) on SU(3):
+      (1) P' = P + eps/2 F(U, P')                      [fixed point]
+      (2) U' = exp(i eps/2 V(U',P')) exp(i eps/2 V(U,P')) U   [fixed point]
+      (3) P'' = P' + eps/2 F(U', P')
+    with F = F_G + F_K and V = M^{-1} P.  Iteration rules: step (1) starts from Q0 and,
+    at iterate Q_i, evaluates F_K and V at (U, Q_i); it stops when max|Q_{i+1}-Q_i| <= fp_tol
+    and keeps V(U, Q_i).  Step (2) starts from exp(i eps V(U,P')) U, evaluates V and F_K at
+    (W_i, P') and stops when max|W_{i+1}-W_i| <= fp_tol, keeping F_K(W_i, P') for step (3).
+    The Lie-Poisson term of the group flow is not included (it changes neither H nor the
+    phase-space volume of the continuous flow); exact volume preservation of this discrete
+    group step: parity unpinned.
+    Returns (U'', P'', next initial guess, iteration counts)."""
+    FG = gauge_force(L, U, beta, c1)
+    Q = Q0
+    for i1 in range(1, fp_maxit + 1):
+        _, FK, V0 = kinetic(L, U, Q, mass, tol)
+        Qn = P + 0.5 * eps * (FG + FK)
+        done = _maxabs(Qn - Q) <= fp_tol
+        Q = Qn
+        if done:
+            break
+    else:
+        raise RuntimeError("oracle: momentum fixed point did not converge")
+    Ph = Q
+    E0 = exp_i(0.5 * eps * V0)
+    W = link_update(L, U, V0, eps)
+    for i2 in range(1, fp_maxit + 1):
+        _, FK1, V1 = kinetic(L, W, Ph, mass, tol)
+        Wn = np.einsum("...ij,...jk->...ik", exp_i(0.5 * eps * V1), np.einsum("...ij,...jk->...ik", E0, U))
+        done = _maxabs(Wn - W) <= fp_tol
+        W = Wn
+        if done:
+            break
+    else:
+        raise RuntimeError("oracle: link fixed point did not converge")
+    FG1 = gauge_force(L, W, beta, c1)
+    P2 = Ph + 0.5 * eps * (FG1 + FK1)
+    Qnext = P2 + 0.5 * eps * (FG1 + FK1)
+    return W, P2, Qnext, (i1, i2)
+
+
+def md_trajectory(L, U, P, tau, nsteps, beta, c1, mass, tol=1e-13, fp_tol=1e-13, fp_maxit=100):
+    """nsteps generalised-leapfrog steps of size tau/nsteps; the first momentum
+    fixed point starts from P + eps/2 F_G(U)."""
+    eps = tau / nsteps
+    Q0 = P + 0.5 * eps * gauge_force(L, U, beta, c1)
+    iters = []
+    for _ in range(nsteps):
+        U, P, Q0, it = leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol, fp_tol, fp_maxit)
+        iters.append(it)
+    return U, P, iters
+
+
+def trajectory(L, U, xi, u, tau, nsteps, beta, c1, mass, tol_md=1e-13, tol_h=1e-13,
+               fp_tol=1e-13, fp_maxit=100, metropolis=True):
+    """One RMHMC trajectory: heatbath P = M^{1/2} xi, H0, MD, H1, accept if u <= exp(-dH)."""
+    P0 = heatbath(L, U, xi, mass, tol_h)
+    H0, T0, S0, _ = hamiltonian(L, U, P0, beta, c1, mass, tol_h)
+    U1, P1, iters = md_trajectory(L, U, P0, tau, nsteps, beta, c1, mass, tol_md, fp_tol, fp_maxit)
+    H1, T1, S1, plaq1 = hamiltonian(L, U1, P1, beta, c1, mass, tol_h)
+    dH = H1 - H0
+    accept = (not metropolis) or (u <= math.exp(-dH) if dH > 0 else True)
+    Uout = U1 if accept else U
+    return {"U": Uout, "U1": U1, "P0": P0, "P1": P1, "H0": H0, "H1": H1, "dH": dH,
+            "T0": T0, "S0": S0, "T1": T1, "S1": S1, "accepted": bool(accept),
+            "plaq": action(L, Uout, beta, c1)[1], "iters": iters}
+
+
+def plain_hmc(L, U, ntraj, beta, seed, tau=1.0, nsteps=20, c1=0.0):
+    """Plain HMC (M = 1) with Philox momenta (stream = trajectory index)."""
+    m = identity_mass()
+    acc = 0
+    for n in range(ntraj):
+        xi = gauss_field(L, seed, n, 0)
+        r = trajectory(L, U, xi, uniform(seed, n), tau, nsteps, beta, c1, m)
+        U = r["U"]
+        acc += r["accepted"]
+    return U, acc

@@ -1,0 +1,126 @@
+"""Pins of the oracle's kinetic force and implicit leapfrog (Sec. 3, Eqs. 5-6)."""
+import math
+
+import numpy as np
+import pytest
+
+import helpers as H
+from oracle import fit
+from paper_2112_04556_gb300 import inputs
+
+L2 = (2, 2, 2, 2)
+
+
+def test_kinetic_force_finite_difference(oracle_lib):
+    """F_K = -dT/dw, T = 1/2 |R(A(U)) P|^2, against central differences (h = 1e-5)
+    along random single-link directions."""
+    L = L2
+    U = inputs.random_links(L, eps=0.5, seed=51)
+    P = inputs.gaussian_fields(L, 1, seed=52)[0]
+    m = fit.mass_term(12, 0.9)
+    T, FK, Vel = oracle_lib.kinetic(L, U, P, m, tol=1e-14)
+    rng = np.random.default_rng(53)
+    h = 1e-5
+    for _ in range(8):
+        y, nu = int(rng.integers(0, 16)), int(rng.integers(0, 4))
+        d = rng.standard_normal(8)
+        vals = []
+        for sgn in (+1, -1):
+            Up = U.copy()
+            Up[y, nu] = H.mm(oracle_lib.exp_i(sgn * h * d), U[y, nu])
+            vals.append(oracle_lib.kinetic(L, Up, P, m, tol=1e-14)[0])
+        fd = -(vals[0] - vals[1]) / (2 * h)
+        an = float(FK[y, nu] @ d)
+        assert abs(fd - an) < 1e-6 * max(1.0, abs(an))
+
+
+def test_kinetic_identity_mass(oracle_lib):
+    L = L2
+    U = inputs.random_links(L, eps=0.5, seed=54)
+    P = inputs.gaussian_fields(L, 1, seed=55)[0]
+    T, FK, Vel = oracle_lib.kinetic(L, U, P, oracle_lib.identity_mass())
+    assert abs(T - 0.5 * np.sum(P * P)) < 1e-12 and np.abs(FK).max() == 0 and np.abs(Vel - P).max() == 0
+
+
+def test_kinetic_force_covariant(oracle_lib):
+    L = (2, 2, 2, 4)
+    V = 32
+    U = inputs.random_links(L, eps=0.5, seed=56)
+    P = inputs.gaussian_fields(L, 1, seed=57)[0]
+    g = inputs.random_su3(V, seed=58)
+    m = fit.mass_term(6, 0.9)
+    T0, F0, V0 = oracle_lib.kinetic(L, U, P, m)
+    T1, F1, V1 = oracle_lib.kinetic(L, H.gauge_transform_links(L, U, g), H.gauge_transform_field(P, g), m)
+    assert abs(T0 - T1) < 1e-11 * T0
+    assert np.abs(F1 - H.gauge_transform_field(F0, g)).max() < 1e-11
+    assert np.abs(V1 - H.gauge_transform_field(V0, g)).max() < 1e-11
+
+
+def test_heatbath_covariance_plane_wave(oracle_lib):
+    """U = 1: P = m(A) R(A) xi acts on a plane wave as m(lam) R(lam) = m^{1/2}(lam)."""
+    L = (4, 4, 4, 4)
+    U = inputs.unit_links(L)
+    m = fit.mass_term(12, 0.9)
+    xi = H.plane_wave(L, (1, 2, 0, 3), 1, 4)
+    P = oracle_lib.heatbath(L, U, xi, m)
+    lam = H.free_eigenvalue(L, (1, 2, 0, 3))
+    assert np.abs(P - math.sqrt(0.1 + 0.9 * lam) * xi).max() < 1e-12
+
+
+def test_reversibility(oracle_lib):
+    """Forward trajectory, momentum flip, forward again returns to the start."""
+    L = L2
+    U = inputs.random_links(L, eps=0.3, seed=61)
+    P = inputs.gaussian_fields(L, 1, seed=62)[0]
+    m = fit.mass_term(12, 0.9)
+    U1, P1, _ = oracle_lib.md_trajectory(L, U, P, 0.4, 4, 6.0, 0.0, m, tol=1e-14)
+    U2, P2, _ = oracle_lib.md_trajectory(L, U1, -P1, 0.4, 4, 6.0, 0.0, m, tol=1e-14)
+    assert np.abs(U2 - U).max() < 1e-11
+    assert np.abs(P2 + P).max() < 1e-10
+
+
+def test_energy_error_scales_as_step_squared(oracle_lib):
+    L = L2
+    U = inputs.random_links(L, eps=0.3, seed=63)
+    P = inputs.gaussian_fields(L, 1, seed=64)[0]
+    m = fit.mass_term(8, 0.9)
+    dH = []
+    for n in (5, 10):
+        H0 = oracle_lib.hamiltonian(L, U, P, 6.0, 0.0, m)[0]
+        U1, P1, _ = oracle_lib.md_trajectory(L, U, P, 0.5, n, 6.0, 0.0, m)
+        dH.append(oracle_lib.hamiltonian(L, U1, P1, 6.0, 0.0, m)[0] - H0)
+    ratio = dH[0] / dH[1]
+    assert 3.0 < ratio < 5.0, dH
+
+
+def test_identity_mass_is_plain_leapfrog(oracle_lib):
+    """M = 1: the implicit scheme reduces to the explicit leapfrog
+    P' = P + eps/2 F(U), U' = exp(i eps P') U, P'' = P' + eps/2 F(U')."""
+    L = (2, 2, 2, 4)
+    U = inputs.random_links(L, eps=0.3, seed=65)
+    P = inputs.gaussian_fields(L, 1, seed=66)[0]
+    eps, n = 0.1, 5
+    Ua, Pa, _ = oracle_lib.md_trajectory(L, U, P, eps * n, n, 6.0, -0.331, oracle_lib.identity_mass())
+    Ub, Pb = U, P
+    for _ in range(n):
+        Ph = Pb + 0.5 * eps * oracle_lib.gauge_force(L, Ub, 6.0, -0.331)
+        Ub = H.mm(oracle_lib.exp_i(eps * Ph), Ub)
+        Pb = Ph + 0.5 * eps * oracle_lib.gauge_force(L, Ub, 6.0, -0.331)
+    assert np.abs(Ua - Ub).max() < 1e-13 and np.abs(Pa - Pb).max() < 1e-12
+
+
+@pytest.mark.slow
+def test_plain_hmc_exp_minus_dH(oracle_lib):
+    """<exp(-dH)> = 1 for an area-preserving reversible integrator (plain HMC, 2^4)."""
+    L = L2
+    U = inputs.random_links(L, eps=0.3, seed=0)
+    U, _ = oracle_lib.plain_hmc(L, U, 20, 6.0, seed=5, tau=1.0, nsteps=10)
+    vals = []
+    for n in range(300):
+        xi = oracle_lib.gauss_field(L, 9, n, 0)
+        r = oracle_lib.trajectory(L, U, xi, oracle_lib.uniform(9, n), 1.0, 6, 6.0, 0.0,
+                                  oracle_lib.identity_mass())
+        U = r["U"]
+        vals.append(math.exp(-r["dH"]))
+    vals = np.array(vals)
+    assert abs(vals.mean() - 1.0) < 4 * vals.std() / math.sqrt(len(vals)) + 1e-3
