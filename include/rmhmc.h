@@ -1,0 +1,269 @@
+/*
+ * rmhmc.h — C ABI of the GB300 (sm_103a) implementation of the data-parallel hot path of
+ * Riemannian manifold HMC for SU(3) lattice gauge theory
+ * (Nguyen, Boyle, Christ, Jang, Jung, "Riemannian manifold hybrid Monte Carlo in lattice QCD",
+ *  LATTICE2021, arXiv:2112.04556).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Lattice   periodic 4D, dims = {Lx, Ly, Lz, Lt}, V = Lx Ly Lz Lt sites,
+ *            site s = x + Lx*(y + Ly*(z + Lz*t)).
+ *  Links     U: complex128 [V][4][3][3] (interleaved re, im doubles, row major), U[s][mu] = U_mu(x).
+ *  Fields    su(3)-valued link fields (momenta, forces, Laplacian operands):
+ *            float64 [nfield][V][4][8] (or float32 where `prec` says so): coefficients p^a of
+ *            P = sum_a p^a T^a, T^a = lambda^a / 2 (Gell-Mann), a = 1..8 stored at 0..7.
+ *            Each of the four components P_mu is an independent operand of the Laplacian.
+ *  Inner product  <X,Y> = sum_{x,mu,a} X^a Y^a.
+ *  Derivative     left multiplication: U_mu(x) -> exp(i w^a T^a) U_mu(x); a force is F^a = -dS/dw^a
+ *                 (Sec. 2, the sentence defining F_G below Eq. 3).
+ *  Operator       A = -Delta_G / 16 (Sec. 2, Eq. 3 with d = 4), spectrum in [0, 1].
+ *
+ *  Memory   All field and link pointers are DEVICE pointers on the context's device, owned by the
+ *           caller; the library never frees them.  Small vectors marked (host) are host memory.
+ *           The context owns its workspace: it is allocated by rmhmc_create or on the first call that
+ *           needs it, and reused afterwards; nothing is allocated inside an iteration loop.
+ *  Streams  Every call takes a cudaStream_t (0 = legacy default stream) and enqueues its work there.
+ *           Calls that return host scalars synchronise that stream before returning.
+ *  Threads  A context is not thread-safe: use one context per host thread / stream.
+ *  Errors   Every entry point returns RMHMC_OK (0) or a negative status.  rmhmc_last_error(ctx) gives
+ *           a message.  On error the contents of output buffers are unspecified, except that
+ *           rmhmc_trajectory leaves U unchanged.
+ *  Links    Compute calls take `const double* U`.  A non-NULL U is imported into the context first
+ *           (canonical -> internal layout, FP64 and FP32 copies); NULL reuses the links imported last.
+ */
+#ifndef RMHMC_H
+#define RMHMC_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* the library is built with hidden visibility; these declarations are its exported interface */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+/* status codes */
+#define RMHMC_OK        0
+#define RMHMC_EINVAL   -1   /* bad argument: NULL pointer, size, shape, alignment, shift <= 0 */
+#define RMHMC_ECUDA    -2   /* a CUDA runtime call failed (message in rmhmc_last_error) */
+#define RMHMC_ENOCONV  -3   /* an iteration (CG, refinement, fixed point) hit its cap */
+#define RMHMC_ENAN     -4   /* NaN or Inf in a reduction (residual, Hamiltonian) */
+#define RMHMC_ETIMEOUT -5   /* a bounded device-side wait gave up */
+#define RMHMC_ENOMEM   -6   /* workspace allocation failed */
+
+/* arithmetic precision of a call */
+#define RMHMC_FP64  0       /* everything in float64 */
+#define RMHMC_FP32  1       /* float32 operands and arithmetic, float64 global sums (lap_apply) */
+#define RMHMC_MIXED 1       /* float32 Krylov / recurrence with float64 reliable updates and sums */
+
+/* link storage used by the stencil: 18 reals, or 12 reals (two rows) with the third row rebuilt
+ * as the complex conjugate of the cross product of the first two */
+#define RMHMC_LINK18 18
+#define RMHMC_LINK12 12
+
+/* operator selector of lap_apply */
+#define RMHMC_OP_A     0    /* A = -Delta_G/16, spectrum in [0,1] */
+#define RMHMC_OP_DELTA 1    /* Delta_G itself */
+
+/* damping of the Chebyshev window expansions */
+#define RMHMC_KERNEL_NONE    0
+#define RMHMC_KERNEL_JACKSON 1
+
+typedef struct rmhmc_ctx rmhmc_ctx;
+
+/* Rational mass term (Sec. 3, Eq. 6): M = R(A)^{-2},
+ *   R(lam) = c + sum_{j<npole} alpha[j] / (lam + sigma[j]),  sigma[j] > 0,
+ * the partial-fraction form of the bracket of Eq. (6) (each quadratic denominator of Eq. 6 gives two
+ * simple poles).  kappa is the slope of the target linear mass m(lam) = (1-kappa) + kappa*lam used by
+ * the momentum heatbath P = m(A) R(A) xi (= M^{1/2} xi to the accuracy of the fit).  npole = 0 and
+ * c = 1 give M = 1 (plain HMC).  alpha and sigma are host arrays. */
+typedef struct {
+    double c;
+    int npole;
+    const double* alpha;
+    const double* sigma;
+    double kappa;
+} rmhmc_mass;
+
+/* RMHMC trajectory parameters (Sec. 3). */
+typedef struct {
+    double beta;        /* gauge coupling */
+    double c1;          /* rectangle coefficient (0: Wilson; -0.331: Iwasaki); c0 = 1 - 8 c1 */
+    rmhmc_mass mass;    /* mass term */
+    double tau;         /* trajectory length */
+    int nsteps;         /* leapfrog steps, eps = tau / nsteps */
+    double tol_md;      /* relative residual of the base Krylov system inside the MD forces */
+    double tol_h;       /* relative residual per shift for the Hamiltonian and the heatbath */
+    double fp_tol;      /* max-norm change that ends each implicit fixed-point iteration */
+    int fp_maxit;       /* cap on fixed-point iterations (RMHMC_ENOCONV beyond it) */
+    int maxiter;        /* cap on Krylov iterations per solve */
+    int prec;           /* RMHMC_FP64 or RMHMC_MIXED */
+    uint64_t seed;      /* Philox key for the heatbath noise and the Metropolis uniform */
+    uint32_t traj_index;/* Philox stream: trajectory number */
+    int metropolis;     /* 1: accept/reject with probability min(1, exp(-dH)); 0: always accept */
+} rmhmc_params;
+
+typedef struct {
+    double dH, H0, H1;  /* Hamiltonian (Eq. 5 without log|M|) before and after the MD */
+    double T0, S0, T1, S1;
+    double plaq;        /* average plaquette ReTr/3 of the output configuration */
+    double u;           /* the uniform used by the Metropolis test */
+    int accepted;
+    int md_solves;      /* Krylov runs inside the MD */
+    long long md_iters; /* Krylov iterations inside the MD */
+    int fp_iters_p;     /* momentum fixed-point iterations, summed over steps */
+    int fp_iters_u;     /* link fixed-point iterations, summed over steps */
+    double max_fp_change;
+} rmhmc_result;
+
+/* ---------------------------------------------------------------------------------------------- */
+/* context                                                                                          */
+/* ---------------------------------------------------------------------------------------------- */
+
+/* Create a context for a lattice of extents dims[4] (each >= 2) on CUDA device `device`.
+ * Allocates the link copies and the reduction scratch.  *out receives the handle. */
+int rmhmc_create(const int dims[4], int device, rmhmc_ctx** out);
+
+/* Free all workspace of the context (NULL is allowed). */
+int rmhmc_destroy(rmhmc_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none); valid until the next call. */
+const char* rmhmc_last_error(const rmhmc_ctx* ctx);
+
+/* Import links U (device, canonical complex128 [V][4][3][3]) into the context: an FP64
+ * structure-of-arrays copy and an FP32 copy (first two rows + third row), Sec. 2 Eq. (3)'s links. */
+int rmhmc_set_links(rmhmc_ctx* ctx, const double* U, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Sec. 2, Eq. (3): the normalised adjoint covariant Laplacian                                       */
+/* ---------------------------------------------------------------------------------------------- */
+
+/* Y = op(X) for nfield fields (device, [nfield][V][4][8], float64 if prec == RMHMC_FP64 else
+ * float32; X and Y must not overlap), with
+ *   Delta X_mu(x) = sum_nu [ U_nu(x) X_mu(x+nu) U_nu(x)^dag + U_nu(x-nu)^dag X_mu(x-nu) U_nu(x-nu)
+ *                            - 2 X_mu(x) ]
+ * (the second term as U^dag X U: the gauge-covariant reading of the printed Eq. 3), op = A = -Delta/16
+ * (RMHMC_OP_A) or Delta (RMHMC_OP_DELTA).  linkfmt: RMHMC_LINK18 or RMHMC_LINK12. */
+int lap_apply(rmhmc_ctx* ctx, const double* U, const void* X, void* Y, int nfield, int prec,
+              int linkfmt, int op, cudaStream_t stream);
+
+/* Link derivative of the Laplacian's bilinear form (adjoint of Eq. 3 with respect to the links):
+ *   G^a_nu(y) = sum_f w[f] d<Z_f, A X_f>/dw^a,   U_nu(y) -> exp(i w^a T^a) U_nu(y),
+ * X, Z device float64 [nfield][V][4][8], w host [nfield], G device float64 [V][4][8] (overwritten).
+ * This is the backward kernel behind the kinetic force and the autograd Laplacian. */
+int lap_link_grad(rmhmc_ctx* ctx, const double* U, const double* X, const double* Z, int nfield,
+                  const double* w, int prec, double* G, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Sec. 2, Eq. (4): Chebyshev band-pass filters and per-mode power spectra                           */
+/* ---------------------------------------------------------------------------------------------- */
+
+/* Moments mu_k(G) = <G, T_k(2A-1) G>, k = 0..degree, of every field G in F (device float64
+ * [nF][V][4][8]) and in the noise set (device float64 [nnoise][V][4][8]; NULL: the library draws
+ * nnoise N(0,1) fields from Philox with key `seed`), all fields in one batched recurrence.  Window w
+ * is [edges[w], edges[w+1]] of eigenvalues of A (host, nwin+1 increasing values in [0,1]); its filter
+ * is B_w = sum_k C[w][k] T_k(2A-1) with C the Chebyshev coefficients of the window's indicator,
+ * damped by Jackson's kernel if kernel == RMHMC_KERNEL_JACKSON.  Outputs (host):
+ *   num[f][w]  = <F_f|B_w|F_f>,
+ *   tr[w]      = mean over noise fields of <eta|B_w|eta>  (Hutchinson estimate of Tr B_w over the
+ *                full [V][4][8] space),
+ *   spec[f][w] = num[f][w] / tr[w]                        (Eq. 4: power per mode),
+ *   moments[(nF+nnoise)][degree+1] (nullable).
+ * prec: RMHMC_FP64, or RMHMC_MIXED (float32 recurrence, float64 moment sums). */
+int cheb_filter_spectrum(rmhmc_ctx* ctx, const double* U, const double* F, int nF,
+                         const double* noise, int nnoise, uint64_t seed, int degree, int nwin,
+                         const double* edges, int kernel, int prec, double* spec, double* num,
+                         double* tr, double* moments, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Sec. 3, Eq. (6): rational mass term via a multishift Krylov solve                                */
+/* ---------------------------------------------------------------------------------------------- */
+
+/* y = c b + sum_j alpha[j] (A + sigma[j])^{-1} b for one field b (device float64 [V][4][8]),
+ * nshift shifts (host sigma[], alpha[], every sigma > 0).  All shifts share one Krylov space
+ * (multishift CG).  Stops when every shift has relative true residual
+ * |b - (A+sigma_j) x_j| / |b| <= tol (checked in float64), or returns RMHMC_ENOCONV after maxiter
+ * Krylov iterations in total.
+ * prec = RMHMC_FP64: float64 throughout.  prec = RMHMC_MIXED: float32 Krylov iterations, then
+ * float64 reliable updates (true residual per shift) with float32 correction solves until tol.
+ * Outputs: y (device float64 [V][4][8]); xs (device float64 [nshift][V][4][8], nullable);
+ * iters (host, nullable) Krylov iterations in total; resid (host [nshift], nullable) final true
+ * relative residuals. */
+int rat_mass_solve(rmhmc_ctx* ctx, const double* U, const double* b, int nshift,
+                   const double* sigma, const double* alpha, double c, double tol, int maxiter,
+                   int prec, double* y, double* xs, int* iters, double* resid, cudaStream_t stream);
+
+/* Momentum heatbath (Sec. 3): P = m(A) R(A) xi with m(A) = (1-kappa) + kappa A, so that P has
+ * covariance M = R^{-2} up to the fit error.  xi, P: device float64 [V][4][8]. */
+int rmhmc_heatbath(rmhmc_ctx* ctx, const double* U, const double* xi, const rmhmc_mass* mass,
+                   double tol, int prec, double* P, cudaStream_t stream);
+
+/* Zolotarev's best relative rational approximation R(lam) ~ m(lam)^{-1/2}, m = (1-kappa) + kappa lam
+ * on lam in [0,1] with npole simple poles (host outputs c, alpha[npole], sigma[npole]); max_rel_err
+ * (nullable) receives max |R m^{1/2} - 1| on a 4096-point grid. */
+int rmhmc_mass_fit(int npole, double kappa, double* c, double* alpha, double* sigma,
+                   double* max_rel_err);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* forces (Sec. 2 below Eq. 3; Sec. 3 below Eq. 5)                                                   */
+/* ---------------------------------------------------------------------------------------------- */
+
+/* Gauge force F^a_mu(x) = -dS/dw^a (device float64 [V][4][8]) for
+ *   S = beta sum_x [ c0 sum_{mu<nu} (1 - ReTr P_{mu nu}/3) + c1 sum_{mu!=nu} (1 - ReTr R_{mu nu}/3) ],
+ * c0 = 1 - 8 c1 (c1 = 0: Wilson plaquette action), R the 1x2 rectangles.  action and plaq (host,
+ * nullable) receive S and the average plaquette ReTr P/3, both summed in float64.
+ * prec: RMHMC_FP64, or RMHMC_FP32 (float32 staples, float64 action). */
+int gauge_force(rmhmc_ctx* ctx, const double* U, double beta, double c1, int prec, double* F,
+                double* action, double* plaq, cudaStream_t stream);
+
+/* Kinetic (mass-term) force F_K = -dT/dw with T = 1/2 <P, M(U)^{-1} P> = 1/2 |R(A) P|^2 (Sec. 3,
+ * the force F_M below Eq. 5).  P device float64 [V][4][8]; F (device, nullable) receives F_K;
+ * Vout (device, nullable) the velocity M^{-1} P; T (host, nullable) the kinetic energy.
+ * tol: relative residual of the base Krylov system. */
+int kinetic_force(rmhmc_ctx* ctx, const double* U, const double* P, const rmhmc_mass* mass,
+                  double tol, int prec, double* F, double* Vout, double* T, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Sec. 3: molecular dynamics and the RMHMC trajectory                                              */
+/* ---------------------------------------------------------------------------------------------- */
+
+/* Gaussian su(3) field (device float64 [V][4][8]): coefficient n = 8 mu + a of site s is the
+ * (n mod 2)-th output of the Box-Muller pair made from Philox4x32-10 block
+ * (counter = {n/2, s, stream_id, tag}, key = {seed lo, seed hi}); uniforms take 53 bits from two words. */
+int rmhmc_gauss_field(rmhmc_ctx* ctx, double* out, uint64_t seed, uint32_t stream_id, uint32_t tag,
+                      cudaStream_t stream);
+
+/* Uout = exp(i eps V) U per link (device canonical links; Uout may equal U); the exponential is the
+ * Cayley-Hamilton form, followed by reunitarisation if reunit != 0. */
+int rmhmc_link_update(rmhmc_ctx* ctx, const double* U, const double* V, double eps, int reunit,
+                      double* Uout, cudaStream_t stream);
+
+/* H = T + S for (U, P) (Eq. 5 without log|M|), with the rational solve at relative residual tol. */
+int rmhmc_hamiltonian(rmhmc_ctx* ctx, const double* U, const double* P, const rmhmc_params* p,
+                      double* H, double* T, double* S, cudaStream_t stream);
+
+/* Molecular dynamics only: p->nsteps generalised-leapfrog steps of size p->tau / p->nsteps on
+ * (U, P) in place (device canonical links, device float64 momenta), with the implicit fixed points
+ * of Sec. 3.  r (nullable) receives the iteration counts. */
+int rmhmc_md(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, rmhmc_result* r,
+             cudaStream_t stream);
+
+/* One RMHMC trajectory on U in place: heatbath P0 = m(A)R(A) xi (xi device float64 [V][4][8], or
+ * NULL: Philox(seed, traj_index, tag 0)), H0, MD, H1, then Metropolis with the uniform from Philox
+ * (seed, traj_index, tag 1) unless p->metropolis == 0.  On rejection U is restored.  P_out
+ * (device, nullable) receives the final momenta of the MD. */
+int rmhmc_trajectory(rmhmc_ctx* ctx, double* U, const double* xi, const rmhmc_params* p,
+                     rmhmc_result* r, double* P_out, cudaStream_t stream);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RMHMC_H */

@@ -58,6 +58,7 @@ def lib():
         I4 = ctypes.POINTER(ctypes.c_int)
         d = ctypes.c_double
         L.orc_lap.argtypes = [I4, P, P, P, ctypes.c_int]
+        L.orc_lap_sites.argtypes = [I4, P, P, P, P, ctypes.c_long]
         L.orc_lap_link_grad.argtypes = [I4, P, P, P, ctypes.c_int, P, P]
         L.orc_action_density.argtypes = [I4, P, d, d, P, P]
         L.orc_gauge_force.argtypes = [I4, P, d, d, P]
@@ -108,6 +109,16 @@ def lap(L, U, X):
     Y = np.empty_like(Xs)
     lib().orc_lap(_dims(L), _p(U), _p(Xs), _p(Y), Xs.shape[0])
     return Y[0] if single else Y
+
+
+def lap_sites(L, U, X, sites):
+    """(A X) at the listed sites only: returns [len(sites), 4, 8]."""
+    U = _c(U, np.complex128)
+    X = _c(X, np.float64)
+    sites = _c(sites, np.int64)
+    Y = np.empty((len(sites), 4, 8))
+    lib().orc_lap_sites(_dims(L), _p(U), _p(X), _p(Y), _p(sites), len(sites))
+    return Y
 
 
 def lap_link_grad(L, U, X, Z, w):

@@ -252,6 +252,28 @@ void orc_lap(const int L[4], const double *U, const double *X, double *Y, int nf
     }
 }
 
+/* A X at a list of sites only (same arithmetic as orc_lap; used to sample large lattices) */
+void orc_lap_sites(const int L[4], const double *U, const double *X, double *Y, const long *sites, long nsites) {
+    init_generators();
+    #pragma omp parallel for schedule(static)
+    for (long i = 0; i < nsites; i++) {
+        long s = sites[i];
+        for (int c = 0; c < 4; c++) {
+            mat3 xc = from_coef(X + 32 * s + 8 * c);
+            mat3 acc = m_zero();
+            for (int nu = 0; nu < 4; nu++) {
+                long sp = shift_site(L, s, nu, +1), sm = shift_site(L, s, nu, -1);
+                mat3 uf = m_load(U + 18 * (4 * s + nu));
+                mat3 ub = m_load(U + 18 * (4 * sm + nu));
+                acc = m_add(acc, m_mul(m_mul(uf, from_coef(X + 32 * sp + 8 * c)), m_dag(uf)));
+                acc = m_add(acc, m_mul(m_mul(m_dag(ub), from_coef(X + 32 * sm + 8 * c)), ub));
+                acc = m_add(acc, m_scale(xc, -2.0));
+            }
+            to_coef(m_scale(acc, -1.0 / 16.0), Y + 32 * i + 8 * c);
+        }
+    }
+}
+
 /* Link derivative of the bilinear form:  G^a(y,nu) = sum_f w_f d<Z_f, A X_f>/dw^a
  * with U_nu(y) -> exp(i w^a T^a) U_nu(y), <X,Y> = sum_{x,mu,a} X^a Y^a.
  * Only two terms of Delta contain U = U_nu(y): the forward hop at y and the

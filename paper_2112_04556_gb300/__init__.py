@@ -1,0 +1,337 @@
+"""Python binding of the RMHMC hot-path library (librmhmc.so, C ABI in include/rmhmc.h).
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of the library.  PyTorch
+provides device memory and streams.  The binding refuses to run if the compiled library is
+missing: there is no CPU fallback.
+
+Layouts (see include/rmhmc.h): links complex128 [V,4,3,3]; su(3) fields float64 (or float32 for
+lap_apply) [nfield,V,4,8] with coefficients in the basis T^a = lambda^a/2; site s = x + Lx(y + Ly(z + Lz t)).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "librmhmc.so")
+_lib = None
+
+OK, EINVAL, ECUDA, ENOCONV, ENAN, ETIMEOUT, ENOMEM = 0, -1, -2, -3, -4, -5, -6
+FP64, FP32, MIXED = 0, 1, 1
+LINK18, LINK12 = 18, 12
+OP_A, OP_DELTA = 0, 1
+KERNEL_NONE, KERNEL_JACKSON = 0, 1
+
+_ERRNAMES = {EINVAL: "EINVAL", ECUDA: "ECUDA", ENOCONV: "ENOCONV", ENAN: "ENAN", ETIMEOUT: "ETIMEOUT",
+             ENOMEM: "ENOMEM"}
+
+
+class RmhmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_ERRNAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Mass(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("npole", ctypes.c_int), ("alpha", ctypes.POINTER(ctypes.c_double)),
+                ("sigma", ctypes.POINTER(ctypes.c_double)), ("kappa", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("c1", ctypes.c_double), ("mass", Mass), ("tau", ctypes.c_double),
+                ("nsteps", ctypes.c_int), ("tol_md", ctypes.c_double), ("tol_h", ctypes.c_double),
+                ("fp_tol", ctypes.c_double), ("fp_maxit", ctypes.c_int), ("maxiter", ctypes.c_int),
+                ("prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("traj_index", ctypes.c_uint32),
+                ("metropolis", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("dH", ctypes.c_double), ("H0", ctypes.c_double), ("H1", ctypes.c_double),
+                ("T0", ctypes.c_double), ("S0", ctypes.c_double), ("T1", ctypes.c_double), ("S1", ctypes.c_double),
+                ("plaq", ctypes.c_double), ("u", ctypes.c_double), ("accepted", ctypes.c_int),
+                ("md_solves", ctypes.c_int), ("md_iters", ctypes.c_longlong), ("fp_iters_p", ctypes.c_int),
+                ("fp_iters_u", ctypes.c_int), ("max_fp_change", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def library_path():
+    return _SO
+
+
+def lib():
+    """Load librmhmc.so (import torch first so that one CUDA context is shared)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_SO):
+        raise RuntimeError("librmhmc.so is not built (run __graft_entry__.build() or "
+                           "python paper_2112_04556_gb300/build.py); no CPU fallback exists")
+    import torch  # noqa: F401  (creates the CUDA runtime before the library's own static runtime)
+    L = ctypes.CDLL(_SO)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    DP = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "rmhmc_create": ([ctypes.POINTER(I), I, ctypes.POINTER(P)], I),
+        "rmhmc_destroy": ([P], I),
+        "rmhmc_last_error": ([P], ctypes.c_char_p),
+        "rmhmc_set_links": ([P, P, P], I),
+        "lap_apply": ([P, P, P, P, I, I, I, I, P], I),
+        "lap_link_grad": ([P, P, P, P, I, DP, I, P, P], I),
+        "cheb_filter_spectrum": ([P, P, P, I, P, I, ctypes.c_uint64, I, I, DP, I, I, DP, DP, DP, DP, P], I),
+        "rat_mass_solve": ([P, P, P, I, DP, DP, D, D, I, I, P, P, ctypes.POINTER(I), DP, P], I),
+        "rmhmc_heatbath": ([P, P, P, ctypes.POINTER(Mass), D, I, P, P], I),
+        "rmhmc_mass_fit": ([I, D, DP, DP, DP, DP], I),
+        "gauge_force": ([P, P, D, D, I, P, DP, DP, P], I),
+        "kinetic_force": ([P, P, P, ctypes.POINTER(Mass), D, I, P, P, DP, P], I),
+        "rmhmc_gauss_field": ([P, P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, P], I),
+        "rmhmc_link_update": ([P, P, P, D, I, P, P], I),
+        "rmhmc_hamiltonian": ([P, P, P, ctypes.POINTER(Params), DP, DP, DP, P], I),
+        "rmhmc_md": ([P, P, P, ctypes.POINTER(Params), ctypes.POINTER(Result), P], I),
+        "rmhmc_trajectory": ([P, P, P, ctypes.POINTER(Params), ctypes.POINTER(Result), P, P], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name, None)
+        if fn is None:
+            continue
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must live on the GPU")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dbl(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Context:
+    """A lattice context on one GPU (wraps rmhmc_create / rmhmc_destroy)."""
+
+    def __init__(self, dims, device=0):
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        self.device = device
+        h = ctypes.c_void_p()
+        arr = (ctypes.c_int * 4)(*self.dims)
+        code = lib().rmhmc_create(arr, int(device), ctypes.byref(h))
+        if code != OK:
+            raise RmhmcError(code, "rmhmc_create failed")
+        self.h = h
+
+    def check(self, code):
+        if code != OK:
+            raise RmhmcError(code, lib().rmhmc_last_error(self.h).decode())
+        return code
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rmhmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _links(U):
+    if U is None:
+        return None
+    import torch
+    if U.dtype == torch.complex128:
+        return _ptr(U)
+    if U.dtype == torch.float64:
+        return _ptr(U)
+    raise ValueError("links must be complex128 [V,4,3,3] (or its float64 view)")
+
+
+def set_links(ctx, U, stream=None):
+    ctx.check(lib().rmhmc_set_links(ctx.h, _links(U), _stream(stream)))
+
+
+def lap_apply(ctx, U, X, Y=None, prec=None, linkfmt=LINK18, op=OP_A, stream=None):
+    """Y = A X (A = -Delta_G/16) or Delta_G X; X float64 or float32 [.., V, 4, 8]."""
+    import torch
+    if prec is None:
+        prec = FP64 if X.dtype == torch.float64 else FP32
+    want = torch.float64 if prec == FP64 else torch.float32
+    if X.dtype != want:
+        raise ValueError("X dtype does not match prec")
+    if Y is None:
+        Y = torch.empty_like(X)
+    nfield = X.numel() // (ctx.V * 32)
+    ctx.check(lib().lap_apply(ctx.h, _links(U), _ptr(X), _ptr(Y), nfield, prec, linkfmt, op, _stream(stream)))
+    return Y
+
+
+def lap_link_grad(ctx, U, X, Z, w, G=None, prec=FP64, stream=None):
+    import torch
+    nfield = X.numel() // (ctx.V * 32)
+    w, wp = _dbl(np.atleast_1d(w))
+    if len(w) != nfield:
+        raise ValueError("one weight per field pair")
+    if G is None:
+        G = torch.empty((ctx.V, 4, 8), dtype=torch.float64, device=X.device)
+    ctx.check(lib().lap_link_grad(ctx.h, _links(U), _ptr(X), _ptr(Z), nfield, wp, prec, _ptr(G), _stream(stream)))
+    return G
+
+
+def cheb_filter_spectrum(ctx, U, F, noise, degree, edges, kernel=KERNEL_JACKSON, prec=FP64, nnoise=None, seed=0,
+                         stream=None):
+    """Per-mode power spectra (Eq. 4).  Returns (spec[nF,nwin], num[nF,nwin], tr[nwin], moments)."""
+    nF = F.numel() // (ctx.V * 32)
+    nn = noise.numel() // (ctx.V * 32) if noise is not None else int(nnoise)
+    edges, ep = _dbl(edges)
+    nwin = len(edges) - 1
+    spec = np.zeros((nF, nwin))
+    num = np.zeros((nF, nwin))
+    tr = np.zeros(nwin)
+    mom = np.zeros((nF + nn, degree + 1))
+    ctx.check(lib().cheb_filter_spectrum(
+        ctx.h, _links(U), _ptr(F), nF, _ptr(noise), nn, int(seed), int(degree), nwin, ep, int(kernel), int(prec),
+        spec.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), num.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), mom.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        _stream(stream)))
+    return spec, num, tr, mom
+
+
+def mass_fit(npole=12, kappa=0.9):
+    """Zolotarev fit R(lam) ~ ((1-kappa) + kappa lam)^{-1/2}: dict(c, alpha, sigma, kappa, err)."""
+    alpha = np.zeros(max(npole, 1))
+    sigma = np.zeros(max(npole, 1))
+    c = ctypes.c_double()
+    err = ctypes.c_double()
+    code = lib().rmhmc_mass_fit(int(npole), float(kappa), ctypes.byref(c),
+                                alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(err))
+    if code != OK:
+        raise RmhmcError(code, "rmhmc_mass_fit failed")
+    return {"c": c.value, "alpha": alpha[:npole], "sigma": sigma[:npole], "kappa": float(kappa), "err": err.value}
+
+
+def _mass_struct(mass):
+    alpha, ap = _dbl(mass["alpha"])
+    sigma, sp = _dbl(mass["sigma"])
+    m = Mass(float(mass["c"]), len(alpha), ap, sp, float(mass.get("kappa", 0.0)))
+    m._keep = (alpha, sigma)
+    return m
+
+
+def rat_mass_solve(ctx, U, b, mass, tol=1e-10, maxiter=2000, prec=FP64, want_xs=False, stream=None):
+    """y = c b + sum_j alpha_j (A + sigma_j)^{-1} b.  Returns (y, xs or None, iters, resid[nshift])."""
+    import torch
+    alpha, ap = _dbl(mass["alpha"])
+    sigma, sp = _dbl(mass["sigma"])
+    n = len(alpha)
+    y = torch.empty_like(b)
+    xs = torch.empty((n,) + tuple(b.shape), dtype=b.dtype, device=b.device) if want_xs else None
+    iters = ctypes.c_int()
+    resid = np.zeros(max(n, 1))
+    ctx.check(lib().rat_mass_solve(ctx.h, _links(U), _ptr(b), n, sp, ap, float(mass["c"]), float(tol), int(maxiter),
+                                   int(prec), _ptr(y), _ptr(xs), ctypes.byref(iters),
+                                   resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)))
+    return y, xs, iters.value, resid[:n]
+
+
+def heatbath(ctx, U, xi, mass, tol=1e-10, prec=FP64, stream=None):
+    import torch
+    m = _mass_struct(mass)
+    P = torch.empty_like(xi)
+    ctx.check(lib().rmhmc_heatbath(ctx.h, _links(U), _ptr(xi), ctypes.byref(m), float(tol), int(prec), _ptr(P),
+                                   _stream(stream)))
+    return P
+
+
+def gauge_force(ctx, U, beta, c1=0.0, prec=FP64, F=None, stream=None):
+    """Returns (F [V,4,8], S, plaquette)."""
+    import torch
+    if F is None:
+        F = torch.empty((ctx.V, 4, 8), dtype=torch.float64, device=U.device)
+    S = ctypes.c_double()
+    pl = ctypes.c_double()
+    ctx.check(lib().gauge_force(ctx.h, _links(U), float(beta), float(c1), int(prec), _ptr(F), ctypes.byref(S),
+                                ctypes.byref(pl), _stream(stream)))
+    return F, S.value, pl.value
+
+
+def kinetic_force(ctx, U, P, mass, tol=1e-12, prec=FP64, want_force=True, want_velocity=True, stream=None):
+    """Returns (F_K or None, V = M^{-1} P or None, T)."""
+    import torch
+    m = _mass_struct(mass)
+    F = torch.empty_like(P) if want_force else None
+    Vel = torch.empty_like(P) if want_velocity else None
+    T = ctypes.c_double()
+    ctx.check(lib().kinetic_force(ctx.h, _links(U), _ptr(P), ctypes.byref(m), float(tol), int(prec), _ptr(F),
+                                  _ptr(Vel), ctypes.byref(T), _stream(stream)))
+    return F, Vel, T.value
+
+
+def gauss_field(ctx, seed, stream_id, tag=0, out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty((ctx.V, 4, 8), dtype=torch.float64, device="cuda:%d" % ctx.device)
+    ctx.check(lib().rmhmc_gauss_field(ctx.h, _ptr(out), int(seed), int(stream_id), int(tag), _stream(stream)))
+    return out
+
+
+def link_update(ctx, U, V, eps, reunit=True, out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty_like(U)
+    ctx.check(lib().rmhmc_link_update(ctx.h, _links(U), _ptr(V), float(eps), int(bool(reunit)), _links(out),
+                                      _stream(stream)))
+    return out
+
+
+def make_params(beta=6.0, c1=0.0, mass=None, tau=1.0, nsteps=20, tol_md=1e-10, tol_h=1e-11, fp_tol=1e-10,
+                fp_maxit=50, maxiter=2000, prec=FP64, seed=0, traj_index=0, metropolis=True):
+    mass = mass if mass is not None else {"c": 1.0, "alpha": [], "sigma": [], "kappa": 0.0}
+    p = Params(float(beta), float(c1), _mass_struct(mass), float(tau), int(nsteps), float(tol_md), float(tol_h),
+               float(fp_tol), int(fp_maxit), int(maxiter), int(prec), int(seed), int(traj_index), int(bool(metropolis)))
+    p._keep = p.mass._keep
+    return p
+
+
+def hamiltonian(ctx, U, P, params, stream=None):
+    H, T, S = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    ctx.check(lib().rmhmc_hamiltonian(ctx.h, _links(U), _ptr(P), ctypes.byref(params), ctypes.byref(H),
+                                      ctypes.byref(T), ctypes.byref(S), _stream(stream)))
+    return H.value, T.value, S.value
+
+
+def md(ctx, U, P, params, stream=None):
+    r = Result()
+    ctx.check(lib().rmhmc_md(ctx.h, _links(U), _ptr(P), ctypes.byref(params), ctypes.byref(r), _stream(stream)))
+    return r.as_dict()
+
+
+def rmhmc_trajectory(ctx, U, params, xi=None, P_out=None, stream=None):
+    r = Result()
+    ctx.check(lib().rmhmc_trajectory(ctx.h, _links(U), _ptr(xi), ctypes.byref(params), ctypes.byref(r),
+                                     _ptr(P_out), _stream(stream)))
+    return r.as_dict()

@@ -1,0 +1,272 @@
+// Shared runtime pieces of the library: context, status handling, lattice geometry, link views,
+// deterministic float64 reductions and the workspace pool.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/rmhmc.h"
+#include "su3.cuh"
+
+namespace rm {
+
+constexpr int kBlock = 128;           // threads per block of the site kernels
+constexpr int kRedSlots = 64;         // reduction slots per context (one per concurrent sum)
+
+// ------------------------------------------------------------------------------------------------
+// lattice geometry
+// ------------------------------------------------------------------------------------------------
+struct Geom {
+    int L[4];
+    int stride[4];
+    int V;
+};
+
+__device__ __forceinline__ void neighbours(const Geom& g, int s, int fwd[4], int bwd[4]) {
+    int r = s;
+#pragma unroll
+    for (int d = 0; d < 4; d++) {
+        const int c = r % g.L[d];
+        r /= g.L[d];
+        fwd[d] = (c == g.L[d] - 1) ? s - c * g.stride[d] : s + g.stride[d];
+        bwd[d] = (c == 0) ? s + (g.L[d] - 1) * g.stride[d] : s - g.stride[d];
+    }
+}
+
+__device__ __forceinline__ void site_coords(const Geom& g, int s, int c[4]) {
+#pragma unroll
+    for (int d = 0; d < 4; d++) { c[d] = s % g.L[d]; s /= g.L[d]; }
+}
+
+// site reached from coordinates c by n steps along direction d (periodic), without changing c
+__device__ __forceinline__ int shifted(const Geom& g, const int c[4], int d, int n) {
+    int s = 0;
+#pragma unroll
+    for (int e = 3; e >= 0; e--) {
+        int ce = c[e];
+        if (e == d) { ce = (ce + n) % g.L[e]; if (ce < 0) ce += g.L[e]; }
+        s = s * g.L[e] + ce;
+    }
+    return s;
+}
+
+// ------------------------------------------------------------------------------------------------
+// internal link layouts
+//   FP64: u64[(mu*9 + 3i + j) * V + s]            double2 (re, im)
+//   FP32: u32a[(mu*3 + r) * V + s]  float4, r=0: (u00,u01) r=1: (u02,u10) r=2: (u11,u12)
+//         u32b[(mu*3 + j) * V + s]  float2, u2j (third row; unused by the 12-real format)
+// ------------------------------------------------------------------------------------------------
+struct Links64 { const double2* u; int V; };
+struct Links32 { const float4* a; const float2* b; int V; };
+
+template <typename T, int LF> struct LinkLoad;
+
+template <int LF> struct LinkLoad<double, LF> {
+    __device__ __forceinline__ static mat3<double> load(const Links64& U, int s, int mu) {
+        mat3<double> m;
+        const int rows = LF == 12 ? 2 : 3;
+#pragma unroll
+        for (int i = 0; i < rows; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const double2 v = __ldg(&U.u[(size_t)(mu * 9 + 3 * i + j) * U.V + s]);
+                m.e[i][j] = cmk(v.x, v.y);
+            }
+        if (LF == 12) {
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+                cplx<double> c = csub(cmul(m.e[0][j1], m.e[1][j2]), cmul(m.e[0][j2], m.e[1][j1]));
+                m.e[2][j] = cconj(c);
+            }
+        }
+        return m;
+    }
+};
+
+template <int LF> struct LinkLoad<float, LF> {
+    __device__ __forceinline__ static mat3<float> load(const Links32& U, int s, int mu) {
+        mat3<float> m;
+        const float4 r0 = __ldg(&U.a[(size_t)(mu * 3 + 0) * U.V + s]);
+        const float4 r1 = __ldg(&U.a[(size_t)(mu * 3 + 1) * U.V + s]);
+        const float4 r2 = __ldg(&U.a[(size_t)(mu * 3 + 2) * U.V + s]);
+        m.e[0][0] = cmk(r0.x, r0.y); m.e[0][1] = cmk(r0.z, r0.w);
+        m.e[0][2] = cmk(r1.x, r1.y); m.e[1][0] = cmk(r1.z, r1.w);
+        m.e[1][1] = cmk(r2.x, r2.y); m.e[1][2] = cmk(r2.z, r2.w);
+        if (LF == 12) {
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+                cplx<float> c = csub(cmul(m.e[0][j1], m.e[1][j2]), cmul(m.e[0][j2], m.e[1][j1]));
+                m.e[2][j] = cconj(c);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const float2 v = __ldg(&U.b[(size_t)(mu * 3 + j) * U.V + s]);
+                m.e[2][j] = cmk(v.x, v.y);
+            }
+        }
+        return m;
+    }
+};
+
+// ------------------------------------------------------------------------------------------------
+// field component access: AoS [V][4][8]
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void load8(const double* p, double* x) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int i = 0; i < 4; i++) { double2 v = __ldg(q + i); x[2 * i] = v.x; x[2 * i + 1] = v.y; }
+}
+__device__ __forceinline__ void load8(const float* p, float* x) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    float4 a = __ldg(q), b = __ldg(q + 1);
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+__device__ __forceinline__ void store8(double* p, const double* x) {
+    double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+    for (int i = 0; i < 4; i++) q[i] = make_double2(x[2 * i], x[2 * i + 1]);
+}
+__device__ __forceinline__ void store8(float* p, const float* x) {
+    float4* q = reinterpret_cast<float4*>(p);
+    q[0] = make_float4(x[0], x[1], x[2], x[3]);
+    q[1] = make_float4(x[4], x[5], x[6], x[7]);
+}
+
+// ------------------------------------------------------------------------------------------------
+// deterministic reductions: every block writes its partial sums to a slot array; the last block
+// to finish (ticket counter) adds them in block order in float64 and writes the result.
+// ------------------------------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N], double* sh /* N * (kBlock/32) */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int n = 0; n < N; n++) {
+        double x = v[n];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[n * (blockDim.x >> 5) + warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int n = 0; n < N; n++) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[n * (blockDim.x >> 5) + w];
+            v[n] = s;
+        }
+    }
+}
+
+// float partials summed within a warp in float, then across warps and blocks in double
+template <int N>
+__device__ __forceinline__ void block_sum_f(float (&v)[N], double* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int n = 0; n < N; n++) {
+        float x = v[n];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[n * (blockDim.x >> 5) + warp] = (double)x;
+    }
+    __syncthreads();
+}
+
+// Called by thread 0 of each block with its N block sums.  partials: [nblocks][N] for this
+// reduction, counter: its ticket.  The last block writes the N totals to out[] and returns true.
+template <int N>
+__device__ __forceinline__ bool grid_sum_finish(const double* v, double* partials, unsigned* counter,
+                                                double* out, int nblocks, int bid) {
+#pragma unroll
+    for (int n = 0; n < N; n++) partials[(size_t)bid * N + n] = v[n];
+    __threadfence();
+    const unsigned ticket = atomicAdd(counter, 1u);
+    if (ticket != (unsigned)(nblocks - 1)) return false;
+    __threadfence();
+    for (int n = 0; n < N; n++) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; b++) s += ((volatile double*)partials)[(size_t)b * N + n];
+        out[n] = s;
+    }
+    *counter = 0u;
+    return true;
+}
+
+// ------------------------------------------------------------------------------------------------
+// buffer of device memory owned by the context
+// ------------------------------------------------------------------------------------------------
+struct DevBuf { void* p = nullptr; size_t bytes = 0; };
+
+}  // namespace rm
+
+// ------------------------------------------------------------------------------------------------
+// the context
+// ------------------------------------------------------------------------------------------------
+struct rmhmc_ctx {
+    int device = 0;
+    rm::Geom g{};
+    std::string err;
+    // links
+    double2* u64 = nullptr;
+    float4* u32a = nullptr;
+    float2* u32b = nullptr;
+    bool links_valid = false;
+    // reductions
+    double* red_partials = nullptr;   // [kRedSlots][max_blocks * 8]
+    unsigned* red_counters = nullptr; // [kRedSlots]
+    double* red_out = nullptr;        // [kRedSlots][8]
+    int max_blocks = 0;
+    double* h_pinned = nullptr;       // pinned host staging (kPinned doubles)
+    // workspace pool
+    std::map<std::string, rm::DevBuf> bufs;
+    size_t num_sms = 0;
+    // pinned upload ring (kRingSlots slots of kRingBytes) and the events that guard slot reuse
+    char* ring = nullptr;
+    cudaEvent_t ring_ev[4] = {};
+    unsigned ring_idx = 0;
+    // events of the look-behind convergence check of the Krylov loop
+    cudaEvent_t kr_ev[2] = {};
+};
+
+namespace rm {
+
+constexpr int kPinned = 1 << 16;
+constexpr int kRingSlots = 4;
+constexpr size_t kRingBytes = 1 << 20;
+// copy host bytes to device memory asynchronously through the pinned ring
+int upload(rmhmc_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st);
+
+int set_err(rmhmc_ctx* ctx, int code, const char* fmt, ...);
+int cuda_check(rmhmc_ctx* ctx, cudaError_t e, const char* what);
+void* workspace(rmhmc_ctx* ctx, const char* name, size_t bytes, int* status);
+int import_links(rmhmc_ctx* ctx, const double* U, cudaStream_t st);
+int ensure_links(rmhmc_ctx* ctx, const double* U, cudaStream_t st);
+inline size_t field_elems(const rmhmc_ctx* ctx) { return (size_t)ctx->g.V * 32; }
+inline int site_blocks(const rmhmc_ctx* ctx) { return (ctx->g.V + kBlock - 1) / kBlock; }
+inline Links64 links64(const rmhmc_ctx* ctx) { return Links64{ctx->u64, ctx->g.V}; }
+inline Links32 links32(const rmhmc_ctx* ctx) { return Links32{ctx->u32a, ctx->u32b, ctx->g.V}; }
+double* red_slot_partials(rmhmc_ctx* ctx, int slot);
+unsigned* red_slot_counter(rmhmc_ctx* ctx, int slot);
+double* red_slot_out(rmhmc_ctx* ctx, int slot);
+// copy n doubles from device to host through pinned memory and synchronise the stream
+int fetch(rmhmc_ctx* ctx, const double* dsrc, double* hdst, int n, cudaStream_t st);
+
+}  // namespace rm
+
+#define RM_CHECK(ctx, call)                                                  \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return rm::cuda_check((ctx), e_, #call);      \
+    } while (0)
+#define RM_LAUNCH_CHECK(ctx) RM_CHECK(ctx, cudaGetLastError())
+#define RM_TRY(x)                     \
+    do {                              \
+        int s_ = (x);                 \
+        if (s_ != RMHMC_OK) return s_; \
+    } while (0)

@@ -1,0 +1,660 @@
+// Krylov engine (see krylov.cuh): CG on the smallest shift keeping the residual basis in HBM,
+// Lanczos post-processing on the host, basis combinations, float64 reliable updates.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "krylov.cuh"
+#include "ops.cuh"
+#include "stencil.cuh"
+
+namespace rm {
+
+constexpr int kSlotGamma = 0, kSlotRho = 1, kSlotNorm = 2, kSlotResid = 8;   // reduction slots
+constexpr int kCheckChunk = 8;                                                 // iterations per flag check
+constexpr int kMaxCombine = 32;                                                // outputs per combine launch
+
+// ------------------------------------------------------------------------------------------------
+// elementwise field kernels (one thread per site, 32 reals)
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_cg_start(const T* __restrict__ b, T* __restrict__ r0, int V, int* flags, double* rho,
+                           double* partials, unsigned* counter) {
+    __shared__ double sh[kBlock / 32];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (s < V) {
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            T x[8];
+            load8(b + (size_t)s * 32 + mu * 8, x);
+            store8(r0 + (size_t)s * 32 + mu * 8, x);
+#pragma unroll
+            for (int k = 0; k < 8; k++) acc += (double)x[k] * (double)x[k];
+        }
+    }
+    double v[1] = {acc};
+    block_sum<1>(v, sh);
+    if (threadIdx.x == 0) {
+        double out[1];
+        if (grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x)) {
+            rho[0] = out[0];
+            flags[1] = 0;
+            flags[0] = isfinite(out[0]) ? (out[0] == 0.0 ? 1 : 0) : 3;
+        }
+    }
+}
+
+// q = (A + sigma0) p_k with p_k = r_k + beta_{k-1} p_{k-1} formed on the fly; gamma_k = <p_k, q>
+template <typename T, int LF>
+__global__ void __launch_bounds__(kBlock) k_cg_A(Geom g, typename LinksOf<T>::type U, const T* __restrict__ r,
+                                                  const T* __restrict__ pold, T* __restrict__ pnew, T* __restrict__ q,
+                                                  T diag, int k, const int* __restrict__ flags, double* vals, int maxit,
+                                                  double* partials, unsigned* counter) {
+    __shared__ double sh[kBlock / 32];
+    if (flags[0]) return;
+    const double* rho = vals;
+    double* gamma = vals + (maxit + 1);
+    double* alpha = gamma + maxit;
+    const double* beta = alpha + maxit;
+    const T b = k > 0 ? (T)beta[k - 1] : T(0);
+    const SrcAxpy<T> src{r, k > 0 ? pold : nullptr, b};
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    T dot = T(0);
+    if (s < g.V) {
+        herm<T> acc[4];
+        hop_sum4<T, LF>(g, U, s, src, acc);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            T h[8], x[8], y[8];
+            herm2_to_coef(acc[mu], h);
+            src(s, mu, x);
+#pragma unroll
+            for (int a = 0; a < 8; a++) {
+                y[a] = fma(T(-0.0625), h[a], diag * x[a]);
+                dot = fma(x[a], y[a], dot);
+            }
+            store8(pnew + (size_t)s * 32 + mu * 8, x);
+            store8(q + (size_t)s * 32 + mu * 8, y);
+        }
+    }
+    double v[1];
+    if (sizeof(T) == 4) {
+        float fv[1] = {(float)dot};
+        block_sum_f<1>(fv, sh);
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kBlock / 32; w++) t += sh[w];
+            v[0] = t;
+        }
+    } else {
+        v[0] = (double)dot;
+        block_sum<1>(v, sh);
+    }
+    if (threadIdx.x == 0) {
+        double out[1];
+        if (grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x)) {
+            gamma[k] = out[0];
+            alpha[k] = rho[k] / out[0];
+        }
+    }
+}
+
+// r_{k+1} = r_k - alpha_k q ; rho_{k+1} = |r_{k+1}|^2 ; convergence flags
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_B(const T* __restrict__ r, T* __restrict__ rn, const T* __restrict__ q,
+                                                  int V, int k, int* flags, double* vals, int maxit, double tol2,
+                                                  double* partials, unsigned* counter) {
+    __shared__ double sh[kBlock / 32];
+    if (flags[0]) return;
+    double* rho = vals;
+    const double* gamma = vals + (maxit + 1);
+    const double* alpha = gamma + maxit;
+    double* beta = (double*)(alpha + maxit);
+    const T a = (T)alpha[k];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    T dot = T(0);
+    if (s < V) {
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            T x[8], y[8];
+            load8(r + (size_t)s * 32 + mu * 8, x);
+            load8(q + (size_t)s * 32 + mu * 8, y);
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                x[c] = fma(-a, y[c], x[c]);
+                dot = fma(x[c], x[c], dot);
+            }
+            store8(rn + (size_t)s * 32 + mu * 8, x);
+        }
+    }
+    double v[1];
+    if (sizeof(T) == 4) {
+        float fv[1] = {(float)dot};
+        block_sum_f<1>(fv, sh);
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kBlock / 32; w++) t += sh[w];
+            v[0] = t;
+        }
+    } else {
+        v[0] = (double)dot;
+        block_sum<1>(v, sh);
+    }
+    if (threadIdx.x == 0) {
+        double out[1];
+        if (grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x)) {
+            const double rr = out[0];
+            rho[k + 1] = rr;
+            beta[k] = rr / rho[k];
+            flags[1] = k + 1;
+            if (!isfinite(rr) || !isfinite(alpha[k]))
+                flags[0] = 3;
+            else if (rr <= tol2 * rho[0])
+                flags[0] = 1;
+            else if (k + 1 >= maxit)
+                flags[0] = 2;
+        }
+    }
+}
+
+// out[m] = sum_k coef[m][k] basis_k, two reals per thread; coefficients staged through shared memory
+template <typename T, typename TO>
+struct OutPtrs { TO* p[kMaxCombine]; };
+
+template <typename T, typename TO>
+__global__ void __launch_bounds__(kBlock) k_combine(const T* __restrict__ R, size_t fs, int n, const double* __restrict__ coef,
+                                                     int M, OutPtrs<T, TO> outs, size_t npair) {
+    constexpr int KC = 64;
+    __shared__ T cs[kMaxCombine * KC];
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    T acc0[kMaxCombine], acc1[kMaxCombine];
+#pragma unroll
+    for (int m = 0; m < kMaxCombine; m++) { acc0[m] = T(0); acc1[m] = T(0); }
+    for (int k0 = 0; k0 < n; k0 += KC) {
+        const int kc = min(KC, n - k0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < M * kc; t += blockDim.x) {
+            const int m = t / kc, kk = t % kc;
+            cs[m * KC + kk] = (T)coef[(size_t)m * n + k0 + kk];
+        }
+        __syncthreads();
+        if (i < npair) {
+            for (int kk = 0; kk < kc; kk++) {
+                T x0, x1;
+                if (sizeof(T) == 4) {
+                    const float2 v = __ldg(reinterpret_cast<const float2*>(R + (size_t)(k0 + kk) * fs) + i);
+                    x0 = (T)v.x; x1 = (T)v.y;
+                } else {
+                    const double2 v = __ldg(reinterpret_cast<const double2*>(R + (size_t)(k0 + kk) * fs) + i);
+                    x0 = (T)v.x; x1 = (T)v.y;
+                }
+#pragma unroll
+                for (int m = 0; m < kMaxCombine; m++)
+                    if (m < M) {
+                        const T c = cs[m * KC + kk];
+                        acc0[m] = fma(c, x0, acc0[m]);
+                        acc1[m] = fma(c, x1, acc1[m]);
+                    }
+            }
+        }
+    }
+    if (i < npair) {
+#pragma unroll
+        for (int m = 0; m < kMaxCombine; m++)
+            if (m < M) {
+                outs.p[m][2 * i] = (TO)acc0[m];
+                outs.p[m][2 * i + 1] = (TO)acc1[m];
+            }
+    }
+}
+
+// r_f = b - (A + sigma_f) x_f, float64, with per-field squared norms
+template <int LF>
+__global__ void __launch_bounds__(kBlock) k_resid64(Geom g, Links64 U, const double* __restrict__ b, const double* __restrict__ x,
+                                                     const double* __restrict__ sig, double* __restrict__ r, size_t fs,
+                                                     double* partials, unsigned* counters, double* out, size_t slot_stride) {
+    __shared__ double sh[kBlock / 32];
+    const int f = blockIdx.y;
+    const double* xf = x + f * fs;
+    const double diag = 0.5 + sig[f];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double nrm = 0.0;
+    if (s < g.V) {
+        herm<double> acc[4];
+        hop_sum4<double, LF>(g, U, s, SrcField<double>{xf}, acc);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            double h[8], xx[8], bb[8], y[8];
+            herm2_to_coef(acc[mu], h);
+            load8(xf + (size_t)s * 32 + mu * 8, xx);
+            load8(b + (size_t)s * 32 + mu * 8, bb);
+#pragma unroll
+            for (int a = 0; a < 8; a++) {
+                y[a] = bb[a] - (diag * xx[a] - 0.0625 * h[a]);
+                nrm = fma(y[a], y[a], nrm);
+            }
+            if (r) store8(r + f * fs + (size_t)s * 32 + mu * 8, y);
+        }
+    }
+    double v[1] = {nrm};
+    block_sum<1>(v, sh);
+    if (threadIdx.x == 0)
+        grid_sum_finish<1>(v, partials + f * slot_stride, counters + f, out + (size_t)f * 8, gridDim.x, blockIdx.x);
+}
+
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+__global__ void k_add_f2d(const float* __restrict__ in, double* __restrict__ out, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] += (double)in[i];
+}
+__global__ void k_axpby64(double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                          double* __restrict__ out, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = a * x[i] + (y ? b * y[i] : 0.0);
+}
+__global__ void k_norm2_64(const double* __restrict__ x, size_t n, double* partials, unsigned* counter, double* out) {
+    __shared__ double sh[kBlock / 32];
+    double acc = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        acc = fma(x[i], x[i], acc);
+    double v[1] = {acc};
+    block_sum<1>(v, sh);
+    if (threadIdx.x == 0) grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x);
+}
+
+static int elem_grid(const rmhmc_ctx* ctx, size_t n) {
+    size_t b = (n + kBlock - 1) / kBlock;
+    const size_t cap = (size_t)ctx->num_sms * 16;
+    return (int)std::max<size_t>(1, std::min(b, cap));
+}
+
+int to_float(rmhmc_ctx* ctx, const double* in, float* out, size_t n, cudaStream_t st) {
+    k_to_float<<<elem_grid(ctx, n), kBlock, 0, st>>>(in, out, n);
+    RM_LAUNCH_CHECK(ctx);
+    return RMHMC_OK;
+}
+int add_float_to_double(rmhmc_ctx* ctx, const float* in, double* out, size_t n, cudaStream_t st) {
+    k_add_f2d<<<elem_grid(ctx, n), kBlock, 0, st>>>(in, out, n);
+    RM_LAUNCH_CHECK(ctx);
+    return RMHMC_OK;
+}
+int axpby64(rmhmc_ctx* ctx, double a, const double* x, double b, const double* y, double* out, size_t n, cudaStream_t st) {
+    k_axpby64<<<elem_grid(ctx, n), kBlock, 0, st>>>(a, x, b, y, out, n);
+    RM_LAUNCH_CHECK(ctx);
+    return RMHMC_OK;
+}
+int norm2_64(rmhmc_ctx* ctx, const double* x, size_t n, double* out, cudaStream_t st) {
+    const int grid = std::min(elem_grid(ctx, n), ctx->max_blocks);
+    k_norm2_64<<<grid, kBlock, 0, st>>>(x, n, red_slot_partials(ctx, kSlotNorm), red_slot_counter(ctx, kSlotNorm),
+                                        red_slot_out(ctx, kSlotNorm));
+    RM_LAUNCH_CHECK(ctx);
+    return fetch(ctx, red_slot_out(ctx, kSlotNorm), out, 1, st);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Lanczos tridiagonal matrix from the CG coefficients
+//   A0 v_k = -(sqrt(beta_{k-1})/alpha_{k-1}) v_{k-1} + (1/alpha_k + beta_{k-1}/alpha_{k-1}) v_k
+//            - (sqrt(beta_k)/alpha_k) v_{k+1},   v_k = r_k / |r_k|
+// ------------------------------------------------------------------------------------------------
+void Tridiag::build(const KrylovResult& kr) {
+    n = kr.n;
+    d.assign(n, 0.0);
+    e.assign(n > 0 ? n - 1 : 0, 0.0);
+    inv_norm.assign(n, 0.0);
+    bnorm = sqrt(kr.rho[0]);
+    for (int k = 0; k < n; k++) {
+        d[k] = 1.0 / kr.alpha[k] + (k > 0 ? kr.beta[k - 1] / kr.alpha[k - 1] : 0.0);
+        if (k < n - 1) e[k] = -sqrt(kr.beta[k]) / kr.alpha[k];
+        inv_norm[k] = 1.0 / sqrt(kr.rho[k]);
+    }
+}
+
+void Tridiag::solve(double shift, const std::vector<double>& rhs, std::vector<double>& y) const {
+    // Thomas algorithm (T + shift is symmetric positive definite)
+    std::vector<double> c(n), dd(n);
+    y.assign(n, 0.0);
+    if (n == 0) return;
+    double den = d[0] + shift;
+    c[0] = n > 1 ? e[0] / den : 0.0;
+    dd[0] = rhs[0] / den;
+    for (int k = 1; k < n; k++) {
+        den = d[k] + shift - e[k - 1] * c[k - 1];
+        c[k] = k < n - 1 ? e[k] / den : 0.0;
+        dd[k] = (rhs[k] - e[k - 1] * dd[k - 1]) / den;
+    }
+    y[n - 1] = dd[n - 1];
+    for (int k = n - 2; k >= 0; k--) y[k] = dd[k] - c[k] * y[k + 1];
+}
+
+void Tridiag::to_basis(const std::vector<double>& y, double* row) const {
+    for (int k = 0; k < n; k++) row[k] = y[k] * inv_norm[k];
+}
+
+// ------------------------------------------------------------------------------------------------
+// the CG run
+// ------------------------------------------------------------------------------------------------
+struct KWork {
+    void* basis = nullptr;
+    void *p0 = nullptr, *p1 = nullptr, *q = nullptr;
+    int* flags = nullptr;
+    double* vals = nullptr;
+    int maxit = 0;
+};
+// the stored basis holds at most kBasisCap residuals: longer runs stop there and the caller's
+// reliable-update loop continues from the true residual (a restart)
+constexpr int kBasisCap = 160;
+
+template <typename T>
+static int krylov_workspace(rmhmc_ctx* ctx, int maxit, KWork& w) {
+    int status = RMHMC_OK;
+    const size_t fb = field_elems(ctx) * sizeof(T);
+    const bool f32 = sizeof(T) == 4;
+    w.basis = workspace(ctx, f32 ? "kr_basis32" : "kr_basis64", fb * (size_t)(maxit + 1), &status);
+    if (!w.basis) return status;
+    w.p0 = workspace(ctx, f32 ? "kr_p0_32" : "kr_p0_64", fb, &status);
+    w.p1 = workspace(ctx, f32 ? "kr_p1_32" : "kr_p1_64", fb, &status);
+    w.q = workspace(ctx, f32 ? "kr_q32" : "kr_q64", fb, &status);
+    void* sc = workspace(ctx, "kr_scal", 64 + sizeof(double) * 4 * (size_t)(maxit + 2), &status);
+    if (!w.p0 || !w.p1 || !w.q || !sc) return status;
+    w.flags = (int*)sc;
+    w.vals = (double*)((char*)sc + 64);
+    w.maxit = maxit;
+    return RMHMC_OK;
+}
+
+template <typename T>
+T* krylov_basis(rmhmc_ctx* ctx) {
+    auto it = ctx->bufs.find(sizeof(T) == 4 ? "kr_basis32" : "kr_basis64");
+    return it == ctx->bufs.end() ? nullptr : (T*)it->second.p;
+}
+
+template <typename T>
+int krylov_run(rmhmc_ctx* ctx, const T* b, double sigma0, double tol, int maxit, KrylovResult& out, cudaStream_t st) {
+    if (maxit < 1) return set_err(ctx, RMHMC_EINVAL, "maxiter must be >= 1");
+    if (!(sigma0 > 0.0)) return set_err(ctx, RMHMC_EINVAL, "shifts must be > 0");
+    maxit = std::min(maxit, kBasisCap);
+    KWork w;
+    RM_TRY(krylov_workspace<T>(ctx, maxit, w));
+    const size_t fs = field_elems(ctx);
+    T* R = (T*)w.basis;
+    const int nb = site_blocks(ctx);
+    k_cg_start<T><<<nb, kBlock, 0, st>>>(b, R, ctx->g.V, w.flags, w.vals, red_slot_partials(ctx, kSlotRho),
+                                         red_slot_counter(ctx, kSlotRho));
+    RM_LAUNCH_CHECK(ctx);
+    typename LinksOf<T>::type U;
+    if constexpr (sizeof(T) == 8) U = links64(ctx); else U = links32(ctx);
+    const T diag = (T)(0.5 + sigma0);
+    const double tol2 = tol * tol;
+    // pinned flag slots for the look-behind convergence check
+    int* hflags = (int*)(ctx->h_pinned + kPinned - 16);
+    cudaEvent_t* ev = ctx->kr_ev;
+    int chunk = 0;
+    bool stop = false;
+    for (int k0 = 0; k0 < maxit && !stop; k0 += kCheckChunk, chunk++) {
+        const int k1 = std::min(maxit, k0 + kCheckChunk);
+        for (int k = k0; k < k1; k++) {
+            const T* r = R + (size_t)k * fs;
+            T* rn = R + (size_t)(k + 1) * fs;
+            T* pold = (T*)((k & 1) ? w.p0 : w.p1);
+            T* pnew = (T*)((k & 1) ? w.p1 : w.p0);
+            if (ctx->g.V > 0) {
+                // the stencil kernel is instantiated per link format; 18-real links throughout the solver
+                k_cg_A<T, 18><<<nb, kBlock, 0, st>>>(ctx->g, U, r, pold, pnew, (T*)w.q, diag, k, w.flags, w.vals, maxit,
+                                                     red_slot_partials(ctx, kSlotGamma), red_slot_counter(ctx, kSlotGamma));
+                k_cg_B<T><<<nb, kBlock, 0, st>>>(r, rn, (const T*)w.q, ctx->g.V, k, w.flags, w.vals, maxit, tol2,
+                                                 red_slot_partials(ctx, kSlotRho), red_slot_counter(ctx, kSlotRho));
+            }
+        }
+        RM_LAUNCH_CHECK(ctx);
+        const int slot = chunk & 1;
+        RM_CHECK(ctx, cudaMemcpyAsync(hflags + 2 * slot, w.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        RM_CHECK(ctx, cudaEventRecord(ev[slot], st));
+        // inspect the previous chunk's flags while this chunk runs
+        if (chunk > 0) {
+            RM_CHECK(ctx, cudaEventSynchronize(ev[slot ^ 1]));
+            if (hflags[2 * (slot ^ 1)] != 0) stop = true;
+        }
+    }
+    RM_CHECK(ctx, cudaMemcpyAsync(hflags, w.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    RM_CHECK(ctx, cudaStreamSynchronize(st));
+    out.status = hflags[0];
+    out.n = hflags[1];
+    if (out.status == 0) out.status = 2;   // ran out of iterations without a flag (maxit reached)
+    const int n = out.n;
+    std::vector<double> buf(3 * (size_t)maxit + 1);
+    // rho[0..n], alpha[0..n-1], beta[0..n-1]
+    if (n + 1 > kPinned - 64) return set_err(ctx, RMHMC_EINVAL, "Krylov run too long for the staging area");
+    RM_TRY(fetch(ctx, w.vals, buf.data(), n + 1, st));
+    out.rho.assign(buf.begin(), buf.begin() + n + 1);
+    out.alpha.resize(n);
+    out.beta.resize(n);
+    if (n > 0) {
+        RM_TRY(fetch(ctx, w.vals + (maxit + 1) + maxit, out.alpha.data(), n, st));
+        RM_TRY(fetch(ctx, w.vals + (maxit + 1) + 2 * maxit, out.beta.data(), n, st));
+    }
+    if (out.status == 3) return set_err(ctx, RMHMC_ENAN, "NaN/Inf in the Krylov recurrence");
+    return RMHMC_OK;
+}
+
+template <typename T, typename TO>
+int krylov_combine(rmhmc_ctx* ctx, const CombineSpec& spec, TO* const* outs, cudaStream_t st) {
+    if (spec.n == 0) {
+        for (int m = 0; m < spec.M; m++) RM_CHECK(ctx, cudaMemsetAsync(outs[m], 0, field_elems(ctx) * sizeof(TO), st));
+        return RMHMC_OK;
+    }
+    int status = RMHMC_OK;
+    const T* R = krylov_basis<T>(ctx);
+    const size_t fs = field_elems(ctx);
+    const size_t npair = fs / 2;
+    for (int m0 = 0; m0 < spec.M; m0 += kMaxCombine) {
+        const int mc = std::min(kMaxCombine, spec.M - m0);
+        double* dcoef = (double*)workspace(ctx, "kr_coef", sizeof(double) * (size_t)kMaxCombine * spec.n, &status);
+        if (!dcoef) return status;
+        RM_TRY(upload(ctx, dcoef, spec.coef.data() + (size_t)m0 * spec.n, sizeof(double) * (size_t)mc * spec.n, st));
+        OutPtrs<T, TO> op{};
+        for (int m = 0; m < mc; m++) op.p[m] = outs[m0 + m];
+        const int grid = (int)((npair + kBlock - 1) / kBlock);
+        k_combine<T, TO><<<grid, kBlock, 0, st>>>(R, fs, spec.n, dcoef, mc, op, npair);
+        RM_LAUNCH_CHECK(ctx);
+    }
+    return RMHMC_OK;
+}
+
+int resid64(rmhmc_ctx* ctx, const double* b, const double* x, int nf, const double* sigma, double* r, double* norm2,
+            cudaStream_t st) {
+    if (nf > kRedSlots - kSlotResid) return set_err(ctx, RMHMC_EINVAL, "too many shifts for one residual launch");
+    int status = RMHMC_OK;
+    double* dsig = (double*)workspace(ctx, "kr_sig", sizeof(double) * 64, &status);
+    if (!dsig) return status;
+    RM_TRY(upload(ctx, dsig, sigma, sizeof(double) * nf, st));
+    const dim3 grid(site_blocks(ctx), nf);
+    k_resid64<18><<<grid, kBlock, 0, st>>>(ctx->g, links64(ctx), b, x, dsig, r, field_elems(ctx),
+                                           red_slot_partials(ctx, kSlotResid), red_slot_counter(ctx, kSlotResid),
+                                           red_slot_out(ctx, kSlotResid), (size_t)ctx->max_blocks * 8);
+    RM_LAUNCH_CHECK(ctx);
+    std::vector<double> tmp((size_t)nf * 8);
+    RM_TRY(fetch(ctx, red_slot_out(ctx, kSlotResid), tmp.data(), nf * 8, st));
+    for (int f = 0; f < nf; f++) norm2[f] = tmp[(size_t)f * 8];
+    return RMHMC_OK;
+}
+
+template int krylov_run<float>(rmhmc_ctx*, const float*, double, double, int, KrylovResult&, cudaStream_t);
+template int krylov_run<double>(rmhmc_ctx*, const double*, double, double, int, KrylovResult&, cudaStream_t);
+template float* krylov_basis<float>(rmhmc_ctx*);
+template double* krylov_basis<double>(rmhmc_ctx*);
+template int krylov_combine<float, float>(rmhmc_ctx*, const CombineSpec&, float* const*, cudaStream_t);
+template int krylov_combine<float, double>(rmhmc_ctx*, const CombineSpec&, double* const*, cudaStream_t);
+template int krylov_combine<double, double>(rmhmc_ctx*, const CombineSpec&, double* const*, cudaStream_t);
+
+// ------------------------------------------------------------------------------------------------
+// mass term parsing and the per-shift solve with float64 reliable updates
+// ------------------------------------------------------------------------------------------------
+int parse_mass(rmhmc_ctx* ctx, const rmhmc_mass* m, MassTerm& out) {
+    if (!m) return set_err(ctx, RMHMC_EINVAL, "null mass term");
+    if (m->npole < 0 || m->npole > 24) return set_err(ctx, RMHMC_EINVAL, "npole must be in [0, 24]");
+    if (m->npole > 0 && (!m->alpha || !m->sigma)) return set_err(ctx, RMHMC_EINVAL, "null pole arrays");
+    out.c = m->c;
+    out.kappa = m->kappa;
+    out.alpha.assign(m->alpha, m->alpha + m->npole);
+    out.sigma.assign(m->sigma, m->sigma + m->npole);
+    for (double s : out.sigma)
+        if (!(s > 0.0)) return set_err(ctx, RMHMC_EINVAL, "every shift must be > 0");
+    return RMHMC_OK;
+}
+
+static double min_shift(const std::vector<double>& s) { return *std::min_element(s.begin(), s.end()); }
+
+// combination rows of the shifted solutions (T + Delta_j)^{-1} e1 |b|
+static void shifted_rows(const Tridiag& tri, const std::vector<double>& sigma, double sigma0, CombineSpec& spec,
+                         std::vector<std::vector<double>>* ys = nullptr) {
+    const int n = tri.n, ns = (int)sigma.size();
+    spec.n = n;
+    spec.M = ns;
+    spec.coef.assign((size_t)ns * n, 0.0);
+    std::vector<double> e1(n, 0.0), y;
+    if (n > 0) e1[0] = tri.bnorm;
+    if (ys) ys->assign(ns, {});
+    for (int j = 0; j < ns; j++) {
+        tri.solve(sigma[j] - sigma0, e1, y);
+        tri.to_basis(y, spec.coef.data() + (size_t)j * n);
+        if (ys) (*ys)[j] = y;
+    }
+}
+
+int solve_shifts(rmhmc_ctx* ctx, const MassTerm& m, const double* b, double tol, int maxiter, int prec, double* xs,
+                 int* iters, double* resid, cudaStream_t st) {
+    const int ns = m.npole();
+    int total = 0;
+    if (ns == 0) {
+        if (iters) *iters = 0;
+        return RMHMC_OK;
+    }
+    const size_t fs = field_elems(ctx);
+    int status = RMHMC_OK;
+    double b2 = 0.0;
+    RM_TRY(norm2_64(ctx, b, fs, &b2, st));
+    if (b2 == 0.0) {
+        RM_CHECK(ctx, cudaMemsetAsync(xs, 0, sizeof(double) * fs * ns, st));
+        if (resid) for (int j = 0; j < ns; j++) resid[j] = 0.0;
+        if (iters) *iters = 0;
+        return RMHMC_OK;
+    }
+    if (!isfinite(b2)) return set_err(ctx, RMHMC_ENAN, "NaN/Inf in the right-hand side");
+    const double s0 = min_shift(m.sigma);
+    const bool mixed = prec != RMHMC_FP64;
+    const double floor32 = 1e-6;
+    std::vector<double*> outs(ns);
+    for (int j = 0; j < ns; j++) outs[j] = xs + (size_t)j * fs;
+    // first pass: one Krylov space for every shift
+    {
+        KrylovResult kr;
+        if (mixed) {
+            float* b32 = (float*)workspace(ctx, "ss_b32", fs * sizeof(float), &status);
+            if (!b32) return status;
+            RM_TRY(to_float(ctx, b, b32, fs, st));
+            RM_TRY(krylov_run<float>(ctx, b32, s0, std::max(0.5 * tol, floor32), maxiter, kr, st));
+        } else {
+            RM_TRY(krylov_run<double>(ctx, b, s0, 0.5 * tol, maxiter, kr, st));
+        }
+        total += kr.n;
+        Tridiag tri;
+        tri.build(kr);
+        CombineSpec spec;
+        shifted_rows(tri, m.sigma, s0, spec);
+        if (mixed) RM_TRY((krylov_combine<float, double>(ctx, spec, outs.data(), st)));
+        else RM_TRY((krylov_combine<double, double>(ctx, spec, outs.data(), st)));
+        if (kr.status == 2 && !mixed) {
+            // fall through to the refinement check, which reports ENOCONV if needed
+        }
+    }
+    // reliable updates: float64 true residuals, corrections per shift
+    double* r = (double*)workspace(ctx, "ss_r", sizeof(double) * fs * ns, &status);
+    float* r32 = mixed ? (float*)workspace(ctx, "ss_r32", sizeof(float) * fs, &status) : nullptr;
+    float* e32 = mixed ? (float*)workspace(ctx, "ss_e32", sizeof(float) * fs, &status) : nullptr;
+    double* e64 = !mixed ? (double*)workspace(ctx, "ss_e64", sizeof(double) * fs, &status) : nullptr;
+    if (!r || (mixed && (!r32 || !e32)) || (!mixed && !e64)) return status;
+    std::vector<double> n2(ns);
+    for (int cycle = 0;; cycle++) {
+        RM_TRY(resid64(ctx, b, xs, ns, m.sigma.data(), r, n2.data(), st));
+        bool all = true;
+        for (int j = 0; j < ns; j++) {
+            const double rel = sqrt(n2[j] / b2);
+            if (resid) resid[j] = rel;
+            if (!isfinite(rel)) return set_err(ctx, RMHMC_ENAN, "NaN/Inf in a true residual");
+            if (rel > tol) all = false;
+        }
+        if (all) break;
+        if (cycle >= 8 || total >= maxiter)
+            return set_err(ctx, RMHMC_ENOCONV, "shifted solve did not reach %g after %d iterations", tol, total);
+        for (int j = 0; j < ns; j++) {
+            const double rel = sqrt(n2[j] / b2);
+            if (rel <= tol) continue;
+            const double want = std::max(0.5 * tol / rel, 1e-15);
+            KrylovResult kr;
+            const double* rj = r + (size_t)j * fs;
+            if (mixed) {
+                RM_TRY(to_float(ctx, rj, r32, fs, st));
+                RM_TRY(krylov_run<float>(ctx, r32, m.sigma[j], std::max(want, floor32), maxiter, kr, st));
+            } else {
+                RM_TRY(krylov_run<double>(ctx, rj, m.sigma[j], want, maxiter, kr, st));
+            }
+            total += kr.n;
+            Tridiag tri;
+            tri.build(kr);
+            CombineSpec spec;
+            shifted_rows(tri, std::vector<double>{m.sigma[j]}, m.sigma[j], spec);
+            if (mixed) {
+                float* o[1] = {e32};
+                RM_TRY((krylov_combine<float, float>(ctx, spec, o, st)));
+                RM_TRY(add_float_to_double(ctx, e32, outs[j], fs, st));
+            } else {
+                double* o[1] = {e64};
+                RM_TRY((krylov_combine<double, double>(ctx, spec, o, st)));
+                RM_TRY(axpby64(ctx, 1.0, outs[j], 1.0, e64, outs[j], fs, st));
+            }
+        }
+    }
+    if (iters) *iters = total;
+    return RMHMC_OK;
+}
+
+}  // namespace rm
+
+using namespace rm;
+
+extern "C" int rat_mass_solve(rmhmc_ctx* ctx, const double* U, const double* b, int nshift, const double* sigma,
+                              const double* alpha, double c, double tol, int maxiter, int prec, double* y, double* xs,
+                              int* iters, double* resid, cudaStream_t stream) {
+    if (!ctx) return RMHMC_EINVAL;
+    ctx->err.clear();
+    if (!b || !y) return set_err(ctx, RMHMC_EINVAL, "rat_mass_solve: null field");
+    if (nshift < 0 || nshift > 24 || (nshift > 0 && (!sigma || !alpha)))
+        return set_err(ctx, RMHMC_EINVAL, "rat_mass_solve: bad shifts");
+    if (!(tol > 0.0) || maxiter < 1) return set_err(ctx, RMHMC_EINVAL, "rat_mass_solve: bad tolerance or maxiter");
+    if (prec != RMHMC_FP64 && prec != RMHMC_MIXED) return set_err(ctx, RMHMC_EINVAL, "rat_mass_solve: bad prec");
+    if ((uintptr_t)b % 16 || (uintptr_t)y % 16 || (uintptr_t)xs % 16)
+        return set_err(ctx, RMHMC_EINVAL, "rat_mass_solve: fields must be 16-byte aligned");
+    rmhmc_mass mm{c, nshift, alpha, sigma, 0.0};
+    MassTerm m;
+    RM_TRY(parse_mass(ctx, &mm, m));
+    RM_TRY(ensure_links(ctx, U, stream));
+    const size_t fs = field_elems(ctx);
+    int status = RMHMC_OK;
+    double* x = xs;
+    if (!x && nshift > 0) {
+        x = (double*)workspace(ctx, "rs_xs", sizeof(double) * fs * nshift, &status);
+        if (!x) return status;
+    }
+    int it = 0;
+    RM_TRY(solve_shifts(ctx, m, b, tol, maxiter, prec, x, &it, resid, stream));
+    // y = c b + sum_j alpha_j x_j (float64)
+    RM_TRY(axpby64(ctx, c, b, 0.0, nullptr, y, fs, stream));
+    for (int j = 0; j < nshift; j++) RM_TRY(axpby64(ctx, 1.0, y, alpha[j], x + (size_t)j * fs, y, fs, stream));
+    if (iters) *iters = it;
+    return RMHMC_OK;
+}

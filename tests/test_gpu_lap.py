@@ -1,0 +1,100 @@
+"""GPU parity of lap_apply (Sec. 2, Eq. 3) against the FP64 oracle on identical seeded inputs.
+Tolerances: float64 paths <= 1e-12 relative L2, float32 paths <= 1e-5."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import dev, host, rel_l2, torch_cuda
+from paper_2112_04556_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = [(0, 18, 1e-12), (0, 12, 1e-12), (1, 18, 1e-5), (1, 12, 1e-5)]
+
+
+def _run(ctx, U_d, X, prec, linkfmt, op=0):
+    import paper_2112_04556_gb300 as rm
+    torch = torch_cuda()
+    Xd = dev(X, torch.float64 if prec == 0 else torch.float32)
+    return host(rm.lap_apply(ctx, U_d, Xd, prec=prec, linkfmt=linkfmt, op=op)).astype(np.float64)
+
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (2, 4, 6, 8), (5, 3, 4, 7), (3, 3, 3, 3)])
+def test_lap_parity_small(L):
+    """Several 128-site tiles and a ragged last tile (5x3x4x7 = 420 sites); odd extents included."""
+    import paper_2112_04556_gb300 as rm
+    U = inputs.random_links(L, eps=0.7, seed=1)
+    X = inputs.gaussian_fields(L, 3, seed=2)
+    ref = oracle.lap(L, U, X)
+    with rm.Context(L) as ctx:
+        Ud = dev(U)
+        for prec, lf, tol in VARIANTS:
+            Y = _run(ctx, Ud, X, prec, lf)
+            assert rel_l2(Y, ref) <= tol, (prec, lf, rel_l2(Y, ref))
+        # Delta itself: Delta = -16 A
+        Y = _run(ctx, Ud, X[0], 0, 18, op=rm.OP_DELTA)
+        assert rel_l2(Y, -16.0 * ref[0]) <= 1e-12
+
+
+def test_lap_free_field_and_reuse_links():
+    """U = 1 plane wave: exact eigenvalue; U = NULL reuses the imported links."""
+    import paper_2112_04556_gb300 as rm
+    torch = torch_cuda()
+    L = (4, 6, 4, 8)
+    from conftest import site_coords
+    k = 2 * np.pi * np.array([1, 2, 0, 3]) / np.array(L)
+    X = np.zeros((int(np.prod(L)), 4, 8))
+    X[:, 3, 7] = np.cos(site_coords(L) @ k)
+    lam = np.sum(np.sin(k / 2) ** 2) / 4
+    with rm.Context(L) as ctx:
+        rm.set_links(ctx, dev(inputs.unit_links(L)))
+        Y = host(rm.lap_apply(ctx, None, dev(X)))
+        assert np.abs(Y - lam * X).max() < 1e-14
+        Y32 = host(rm.lap_apply(ctx, None, dev(X, torch.float32), prec=rm.FP32, linkfmt=12))
+        assert np.abs(Y32 - lam * X).max() < 1e-6
+
+
+def test_lap_parity_16_4():
+    import paper_2112_04556_gb300 as rm
+    L = (16, 16, 16, 16)
+    U = inputs.random_links(L, eps=0.3, seed=0)
+    X = inputs.gaussian_fields(L, 1, seed=3)[0]
+    ref = oracle.lap(L, U, X)
+    with rm.Context(L) as ctx:
+        Ud = dev(U)
+        for prec, lf, tol in VARIANTS:
+            assert rel_l2(_run(ctx, Ud, X, prec, lf), ref) <= tol
+
+
+@pytest.mark.parametrize("L", [(32, 32, 32, 32), (24, 24, 24, 48)])
+def test_lap_parity_full_size_sampled(L):
+    """Full-size lattices, every variant, compared on 4096 sampled sites."""
+    import paper_2112_04556_gb300 as rm
+    U = inputs.random_links(L, eps=0.3, seed=0)
+    X = inputs.gaussian_fields(L, 1, seed=4)[0]
+    rng = np.random.default_rng(5)
+    V = int(np.prod(L))
+    sites = np.unique(np.concatenate([rng.integers(0, V, 4000), [0, V - 1], np.arange(V - 64, V)]))
+    ref = oracle.lap_sites(L, U, X, sites)
+    with rm.Context(L) as ctx:
+        Ud = dev(U)
+        for prec, lf, tol in VARIANTS:
+            Y = _run(ctx, Ud, X, prec, lf)
+            assert rel_l2(Y[sites], ref) <= tol, (prec, lf)
+
+
+def test_lap_errors_and_empty():
+    import paper_2112_04556_gb300 as rm
+    torch = torch_cuda()
+    L = (4, 4, 4, 4)
+    with rm.Context(L) as ctx:
+        X = torch.zeros((2, 256, 4, 8), dtype=torch.float64, device="cuda")
+        with pytest.raises(rm.RmhmcError):           # no links imported yet
+            rm.lap_apply(ctx, None, X[0])
+        rm.set_links(ctx, dev(inputs.unit_links(L)))
+        with pytest.raises(rm.RmhmcError):           # overlapping input and output
+            rm.lap_apply(ctx, None, X[0], Y=X[0])
+        with pytest.raises(rm.RmhmcError):           # bad link format
+            rm.lap_apply(ctx, None, X[0], linkfmt=9)
+        code = rm.lib().lap_apply(ctx.h, None, rm._ptr(X), rm._ptr(X[1]), 0, 0, 18, 0, rm._stream())
+        assert code == rm.OK                          # nothing to do for zero fields
