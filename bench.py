@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the RMHMC hot path on GB300.
+
+Workload (32^4 full RMHMC): periodic 32^4 lattice, Wilson beta = 6.0, 12-pole mass term with
+kappa = 0.9, tau = 1 with 20 implicit-leapfrog steps, kinetic + gauge forces, Metropolis in float64,
+mixed precision (float32 Krylov, float64 link update, reductions and Hamiltonian).  One step = one
+trajectory followed by the per-mode power spectrum of the new configuration's Wilson and Iwasaki
+gauge forces (degree-200 Chebyshev filters over 64 windows, 16 noise vectors, one batched launch per
+recurrence step).  Links: seeded random start exp(i 0.3 sum r_a T_a), thermalised by plain HMC before
+timing.  Every input is synthetic; the working set (~30 GB) exceeds the 126 MB L2, so no flush is
+needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the float64 CPU oracle instead.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Laplacian GB/s & % HBM peak; RMHMC traj/s at 32^4, mixed vs FP64 at fixed ΔH"
+DIMS = (32, 32, 32, 32)
+BETA = 6.0
+KAPPA = 0.9
+NPOLE = 12
+TAU = 1.0
+NSTEPS = 20
+CHEB_DEGREE = 200
+CHEB_WINDOWS = 64
+CHEB_NOISE = 16
+IWASAKI_C1 = -0.331
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def max_over_ranks(x, dist, device="cpu"):
+    """Largest value of x over all ranks (the timed region of the slowest replica)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seeds(rank):
+    """Per-replica seeds: link start, thermalisation momenta, trajectory momenta."""
+    return {"links": rank, "therm": 7 + rank, "traj": 100 + rank}
+
+
+def oracle_sample(seconds_cap=30.0):
+    """Time the float64 CPU oracle on a bounded sample of the workload: one kinetic-force evaluation
+    (two 12-shift rational solves by per-shift CG, plus the link gradient) and one Laplacian
+    application at 8^4 with the workload's mass term and link recipe."""
+    import numpy as np
+
+    import oracle
+    from oracle import fit
+    from paper_2112_04556_gb300 import inputs
+    oracle.build()
+    L = (8, 8, 8, 8)
+    U = inputs.random_links(L, eps=0.3, seed=0)
+    P = inputs.gaussian_fields(L, 1, seed=1)[0]
+    m = fit.mass_term(NPOLE, KAPPA)
+    t0 = time.perf_counter()
+    oracle.kinetic(L, U, P, m, tol=1e-6)
+    t_kin = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    nlap = 0
+    while time.perf_counter() - t0 < 2.0:
+        oracle.lap(L, U, P)
+        nlap += 1
+    t_lap = (time.perf_counter() - t0) / nlap
+    return {"t_kin_8": t_kin, "t_lap_8": t_lap, "cores": oracle.num_threads(),
+            "scale": float(np.prod(DIMS)) / float(np.prod(L))}
+
+
+def oracle_traj_seconds(s, md_solves):
+    """Oracle seconds per step at 32^4, scaled linearly in volume (iteration counts do not depend on the
+    volume at fixed condition number): (md_solves + 3) kinetic-equivalents for the trajectory (MD plus
+    heatbath and the two Hamiltonians) and (18 fields x 100 applications) for the spectrum."""
+    return s["scale"] * ((md_solves + 3) * s["t_kin_8"] + 18 * CHEB_DEGREE // 2 * s["t_lap_8"])
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    s0 = time.perf_counter()
+    vals = []
+    md_solves = 150   # kinetic evaluations of one 20-step trajectory (the mixed GPU run measures ~150)
+    for i in range(args.warmup + args.steps):
+        s = oracle_sample()
+        if i >= args.warmup:
+            vals.append(oracle_traj_seconds(s, md_solves))
+    sec = sum(vals) / len(vals)
+    value = 1.0 / sec
+    sample = ("oracle kinetic-force evaluation + Laplacian at 8^4 per step, scaled by V(32^4)/V(8^4)=256 and "
+              "by %d kinetic evaluations + 3 (heatbath, 2 Hamiltonians) + 1800 spectrum applications" % md_solves)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "traj/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "32^4 full RMHMC (beta 6.0, 12-pole mass kappa 0.9, tau 1, 20 steps) + "
+                                   "gauge-force spectrum (degree 200, 64 windows)", "lattice": "32^4"},
+            "cpu_baseline": {"value": value, "unit": "traj/s", "cores": s["cores"], "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "traj/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - s0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison trajectory")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--dims", default="32,32,32,32")
+    ap.add_argument("--nsteps", type=int, default=NSTEPS)
+    ap.add_argument("--therm", type=int, default=20, help="plain-HMC thermalisation trajectories")
+    args = ap.parse_args()
+    global DIMS
+    DIMS = tuple(int(v) for v in args.dims.split(","))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    # the CPU oracle sample runs before any GPU work (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample()
+
+    import numpy as np
+    import torch
+
+    import paper_2112_04556_gb300 as rm
+    from paper_2112_04556_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    V = int(np.prod(DIMS))
+    lat = rm.Context(DIMS, device=local)
+    mass = rm.mass_fit(NPOLE, KAPPA)
+    seeds = replica_seeds(rank)
+    U = torch.from_numpy(inputs.random_links(DIMS, eps=0.3, seed=seeds["links"])).cuda()
+
+    # thermalise with plain HMC, every trajectory accepted (not timed)
+    ident = {"c": 1.0, "alpha": [], "sigma": [], "kappa": 0.0}
+    therm = []
+    for n in range(args.therm):
+        p = rm.make_params(beta=BETA, mass=ident, tau=1.0, nsteps=20, tol_md=1e-6, tol_h=1e-11, fp_tol=1e-6,
+                           prec=rm.MIXED, seed=seeds["therm"], traj_index=1000 + n, metropolis=False)
+        therm.append(rm.rmhmc_trajectory(lat, U, p)["plaq"])
+
+    def params(idx, prec):
+        return rm.make_params(beta=BETA, mass=mass, tau=TAU, nsteps=args.nsteps,
+                              tol_md=1e-6 if prec == rm.MIXED else 1e-10, tol_h=1e-11,
+                              fp_tol=1e-6 if prec == rm.MIXED else 1e-10, fp_maxit=50, maxiter=400, prec=prec,
+                              seed=seeds["traj"], traj_index=idx, metropolis=True)
+
+    F2 = torch.empty((2, V, 4, 8), dtype=torch.float64, device="cuda")
+    edges = inputs.equal_windows(CHEB_WINDOWS)
+    results = []
+
+    def step(idx, Ulinks):
+        r = rm.rmhmc_trajectory(lat, Ulinks, params(idx, rm.MIXED))
+        rm.gauge_force(lat, None, BETA, 0.0, prec=rm.FP32, F=F2[0])
+        rm.gauge_force(lat, None, BETA, IWASAKI_C1, prec=rm.FP32, F=F2[1])
+        spec = rm.cheb_filter_spectrum(lat, None, F2, None, CHEB_DEGREE, edges, prec=rm.MIXED,
+                                       nnoise=CHEB_NOISE, seed=idx)[0]
+        r["spec_low"] = float(spec[0, 0])
+        r["spec_high"] = float(spec[0, -1])
+        return r
+
+    U_start = U.clone()
+    for w in range(args.warmup):
+        step(w, U)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    rm.counters(lat, reset=True)
+    rm.set_profiling(lat, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        results.append(step(args.warmup + k, U))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    rm.set_profiling(lat, False)
+    ms = e0.elapsed_time(e1)
+    cnt = rm.counters(lat, reset=True)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = world * args.steps / (ms / 1e3)
+
+    # live roofline of the conjugate-gradient stencil (float32, 18-real links):
+    # per site 4 field passes of 128 B (read r_k, p_{k-1}; write p_k, q_k) + 4 links x 72 B = 800 B
+    peak, peak_kind = measured_peaks()
+    cg_bytes = 800.0 * V
+    cg_avg_ms = cnt["cg_ms"] / max(cnt["cg_count"], 1)
+    achieved = cg_bytes / (cg_avg_ms * 1e-3) / 1e9 if cnt["cg_count"] else None
+    alu_fma = 5000.0 * V   # per site: 8 hops x 4 components x 144 FMA + the fused axpy and epilogue
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None, "peak_kind": peak_kind,
+                "kernel": "k_cg_A<float,18> (CG stencil)", "launches": cnt["cg_count"],
+                "avg_launch_ms": cg_avg_ms, "alu_tfma_s": alu_fma / (cg_avg_ms * 1e-3) / 1e12 if cnt["cg_count"] else None,
+                "alu_peak_tfma_s": 37.4}
+
+    # end to end through the public API with host buffers: pinned H2D of the links, D2H of the result
+    e2e = None
+    if not args.no_e2e:
+        Uh = U.cpu().pin_memory()
+        Uout = torch.empty_like(Uh).pin_memory()
+        Ud = torch.empty_like(U)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            Ud.copy_(Uh, non_blocking=True)
+            step(10000 + k, Ud)
+            Uout.copy_(Ud, non_blocking=True)
+            torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        sec = max_over_ranks(sec, dist, "cuda")
+        nb = Uh.numel() * Uh.element_size()
+        e2e = {"value": world * args.steps / sec, "unit": "traj/s", "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb + 8 * 16}
+
+    # mixed vs float64 at fixed dH: both from the same links and momenta
+    fp64 = None
+    if world == 1 and not args.no_fp64:
+        Ua, Ub = U_start.clone(), U_start.clone()
+        t0 = time.perf_counter()
+        ra = rm.rmhmc_trajectory(lat, Ua, params(0, rm.FP64))
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        rb = rm.rmhmc_trajectory(lat, Ub, params(0, rm.MIXED))
+        fp64 = {"traj_per_s_fp64": 1.0 / t64, "dH_fp64": ra["dH"], "dH_mixed": rb["dH"],
+                "abs_dH_diff": abs(ra["dH"] - rb["dH"]), "plaq_fp64": ra["plaq"], "plaq_mixed": rb["plaq"],
+                "md_iters_fp64": ra["md_iters"], "md_iters_mixed": rb["md_iters"]}
+
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": "traj/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "32^4 full RMHMC (Wilson beta 6.0, 12-pole mass kappa 0.9, tau 1, %d steps, "
+                                   "mixed precision) + gauge-force spectrum (degree 200, 64 windows, 16 noise)"
+                                   % args.nsteps,
+                       "lattice": "x".join(str(d) for d in DIMS), "l2": "working set > L2, no flush",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "thermalisation_plaq": therm[-3:] if therm else None,
+            "roofline": roofline, "clocks": clk, "gpu_launches": cnt["launches"],
+            "krylov_iters": cnt["krylov_iters"], "e2e": e2e,
+            "trajectories": [{k: r[k] for k in ("dH", "accepted", "plaq", "md_solves", "md_iters", "fp_iters_p",
+                                                "fp_iters_u", "spec_low", "spec_high")} for r in results]}
+    if fp64:
+        line["fp64_compare"] = fp64
+    if cpu:
+        md_solves = int(np.mean([r["md_solves"] for r in results]))
+        sec = oracle_traj_seconds(cpu, md_solves)
+        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "traj/s", "cores": cpu["cores"], "kind": "oracle",
+                                "sample": "oracle kinetic-force evaluation (%.1f s) and Laplacian at 8^4, scaled by "
+                                          "V(32^4)/V(8^4) = 256 and by %d + 3 kinetic evaluations + 1800 spectrum "
+                                          "applications per step" % (cpu["t_kin_8"], md_solves)}
+    print(json.dumps(line), flush=True)
+    lat.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

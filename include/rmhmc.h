@@ -138,6 +138,14 @@ const char* rmhmc_last_error(const rmhmc_ctx* ctx);
  * structure-of-arrays copy and an FP32 copy (first two rows + third row), Sec. 2 Eq. (3)'s links. */
 int rmhmc_set_links(rmhmc_ctx* ctx, const double* U, cudaStream_t stream);
 
+/* Counters of the context (host scalars, each pointer nullable): kernels launched by the library,
+ * Krylov iterations, and -- while profiling is on -- the number and summed duration (ms, CUDA events
+ * on the caller's stream) of the conjugate-gradient stencil launches that did work (the matvec that
+ * dominates the trajectory).  reset != 0 zeroes the counters after reading them. */
+int rmhmc_set_profiling(rmhmc_ctx* ctx, int on);
+int rmhmc_get_counters(rmhmc_ctx* ctx, long long* launches, long long* krylov_iters, long long* cg_count,
+                       double* cg_ms, int reset);
+
 /* ---------------------------------------------------------------------------------------------- */
 /* Sec. 2, Eq. (3): the normalised adjoint covariant Laplacian                                       */
 /* ---------------------------------------------------------------------------------------------- */

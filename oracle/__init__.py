@@ -62,6 +62,7 @@ def lib():
         L.orc_lap_link_grad.argtypes = [I4, P, P, P, ctypes.c_int, P, P]
         L.orc_action_density.argtypes = [I4, P, d, d, P, P]
         L.orc_gauge_force.argtypes = [I4, P, d, d, P]
+        L.orc_gauge_force_sites.argtypes = [I4, P, d, d, P, ctypes.c_long, P]
         L.orc_link_update.argtypes = [I4, P, d, P, P]
         L.orc_exp_i.argtypes = [ctypes.c_long, P, P]
         L.orc_mat_mul.argtypes = [ctypes.c_long, P, P, P]
@@ -164,6 +165,15 @@ def gauge_force(L, U, beta, c1=0.0):
     U = _c(U, np.complex128)
     F = np.empty((volume(L), 4, 8))
     lib().orc_gauge_force(_dims(L), _p(U), float(beta), float(c1), _p(F))
+    return F
+
+
+def gauge_force_sites(L, U, beta, c1, sites):
+    """The gauge force at the listed sites only: [len(sites), 4, 8]."""
+    U = _c(U, np.complex128)
+    sites = _c(sites, np.int64)
+    F = np.empty((len(sites), 4, 8))
+    lib().orc_gauge_force_sites(_dims(L), _p(U), float(beta), float(c1), _p(sites), len(sites), _p(F))
     return F
 
 
@@ -377,7 +387,7 @@ def _maxabs(a):
     return float(np.max(np.abs(a))) if a.size else 0.0
 
 
-def leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol=1e-13, fp_tol=1e-13, fp_maxit=100):
+def leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol=1e-13, fp_tol=1e-13, fp_maxit=100, FG=None):
     """One generalised-leapfrog step (Sec. 3; Girolami & Calderhead) on SU(3):
       (1) P' = P + eps/2 F(U, P')                      [fixed point]
       (2) U' = exp(i eps/2 V(U',P')) exp(i eps/2 V(U,P')) U   [fixed point]
@@ -389,8 +399,10 @@ def leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol=1e-13, fp_tol=1e-13, fp_
     The Lie-Poisson term of the group flow is not included (it changes neither H nor the
     phase-space volume of the continuous flow); exact volume preservation of this discrete
     group step: parity unpinned.
-    Returns (U'', P'', next initial guess, iteration counts)."""
-    FG = gauge_force(L, U, beta, c1)
+    FG (optional) is F_G(U) if the caller has it.
+    Returns (U'', P'', next initial guess, iteration counts, F_G(U''))."""
+    if FG is None:
+        FG = gauge_force(L, U, beta, c1)
     Q = Q0
     for i1 in range(1, fp_maxit + 1):
         _, FK, V0 = kinetic(L, U, Q, mass, tol)
@@ -402,11 +414,11 @@ def leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol=1e-13, fp_tol=1e-13, fp_
     else:
         raise RuntimeError("oracle: momentum fixed point did not converge")
     Ph = Q
-    E0 = exp_i(0.5 * eps * V0)
+    E0U = np.matmul(exp_i(0.5 * eps * V0), U)
     W = link_update(L, U, V0, eps)
     for i2 in range(1, fp_maxit + 1):
         _, FK1, V1 = kinetic(L, W, Ph, mass, tol)
-        Wn = np.einsum("...ij,...jk->...ik", exp_i(0.5 * eps * V1), np.einsum("...ij,...jk->...ik", E0, U))
+        Wn = np.matmul(exp_i(0.5 * eps * V1), E0U)
         done = _maxabs(Wn - W) <= fp_tol
         W = Wn
         if done:
@@ -416,17 +428,18 @@ def leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol=1e-13, fp_tol=1e-13, fp_
     FG1 = gauge_force(L, W, beta, c1)
     P2 = Ph + 0.5 * eps * (FG1 + FK1)
     Qnext = P2 + 0.5 * eps * (FG1 + FK1)
-    return W, P2, Qnext, (i1, i2)
+    return W, P2, Qnext, (i1, i2), FG1
 
 
 def md_trajectory(L, U, P, tau, nsteps, beta, c1, mass, tol=1e-13, fp_tol=1e-13, fp_maxit=100):
     """nsteps generalised-leapfrog steps of size tau/nsteps; the first momentum
     fixed point starts from P + eps/2 F_G(U)."""
     eps = tau / nsteps
-    Q0 = P + 0.5 * eps * gauge_force(L, U, beta, c1)
+    FG = gauge_force(L, U, beta, c1)
+    Q0 = P + 0.5 * eps * FG
     iters = []
     for _ in range(nsteps):
-        U, P, Q0, it = leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol, fp_tol, fp_maxit)
+        U, P, Q0, it, FG = leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol, fp_tol, fp_maxit, FG)
         iters.append(it)
     return U, P, iters
 
@@ -446,13 +459,14 @@ def trajectory(L, U, xi, u, tau, nsteps, beta, c1, mass, tol_md=1e-13, tol_h=1e-
             "plaq": action(L, Uout, beta, c1)[1], "iters": iters}
 
 
-def plain_hmc(L, U, ntraj, beta, seed, tau=1.0, nsteps=20, c1=0.0):
-    """Plain HMC (M = 1) with Philox momenta (stream = trajectory index)."""
+def plain_hmc(L, U, ntraj, beta, seed, tau=1.0, nsteps=20, c1=0.0, metropolis=True):
+    """Plain HMC (M = 1) with Philox momenta (stream = trajectory index).  metropolis=False accepts
+    every trajectory (thermalisation from an ordered start, where dH is far from O(1))."""
     m = identity_mass()
     acc = 0
     for n in range(ntraj):
         xi = gauss_field(L, seed, n, 0)
-        r = trajectory(L, U, xi, uniform(seed, n), tau, nsteps, beta, c1, m)
+        r = trajectory(L, U, xi, uniform(seed, n), tau, nsteps, beta, c1, m, metropolis=metropolis)
         U = r["U"]
         acc += r["accepted"]
     return U, acc

@@ -375,44 +375,57 @@ void orc_action_density(const int L[4], const double *U, double beta, double c1,
  * through the link: if it passes forward, W = A U B and d ReTr W = ReTr(i T U B A);
  * if backward, W = A U^dag B and d ReTr W = ReTr(-i T B A U^dag).
  * Hence F = (beta w / 3) * sum over occurrences of those derivatives. */
+static void gauge_force_link(const int L[4], const double *U, const shape_t *sh, int ns, double beta,
+                             long y, int mu, double *out) {
+    double f[8] = {0};
+    mat3 u = m_load(U + 18 * (4 * y + mu));
+    for (int k = 0; k < ns; k++) {
+        for (int i = 0; i < sh[k].n; i++) {
+            int code = sh[k].step[i];
+            int d = (code > 0 ? code : -code) - 1;
+            if (d != mu) continue;
+            /* displacement of steps 0..i-1 */
+            int disp[4] = {0, 0, 0, 0};
+            for (int j = 0; j < i; j++) {
+                int cj = sh[k].step[j];
+                disp[(cj > 0 ? cj : -cj) - 1] += (cj > 0 ? 1 : -1);
+            }
+            /* start site: forward step i starts at y; backward step i ends at y */
+            long x = (code > 0) ? y : shift_site(L, y, mu, +1);
+            for (int e = 0; e < 4; e++) x = shift_site(L, x, e, -disp[e]);
+            long pos = x;
+            mat3 A = m_unit(), B = m_unit();
+            for (int j = 0; j < i; j++) A = m_mul(A, link_step(L, U, &pos, sh[k].step[j]));
+            (void)link_step(L, U, &pos, code);
+            for (int j = i + 1; j < sh[k].n; j++) B = m_mul(B, link_step(L, U, &pos, sh[k].step[j]));
+            double g[8];
+            if (code > 0) deriv_coef(m_mul(m_mul(u, B), A), g);
+            else deriv_coef(m_scale(m_mul(m_mul(B, A), m_dag(u)), -1.0), g);
+            for (int a = 0; a < 8; a++) f[a] += beta * sh[k].w / 3.0 * g[a];
+        }
+    }
+    for (int a = 0; a < 8; a++) out[a] = f[a];
+}
+
 void orc_gauge_force(const int L[4], const double *U, double beta, double c1, double *F) {
     init_generators();
     shape_t sh[64];
     int ns = make_shapes(c1, sh);
     long V = volume(L);
     #pragma omp parallel for schedule(static)
-    for (long y = 0; y < V; y++) {
-        for (int mu = 0; mu < 4; mu++) {
-            double f[8] = {0};
-            mat3 u = m_load(U + 18 * (4 * y + mu));
-            for (int k = 0; k < ns; k++) {
-                for (int i = 0; i < sh[k].n; i++) {
-                    int code = sh[k].step[i];
-                    int d = (code > 0 ? code : -code) - 1;
-                    if (d != mu) continue;
-                    /* displacement of steps 0..i-1 */
-                    int disp[4] = {0, 0, 0, 0};
-                    for (int j = 0; j < i; j++) {
-                        int cj = sh[k].step[j];
-                        disp[(cj > 0 ? cj : -cj) - 1] += (cj > 0 ? 1 : -1);
-                    }
-                    /* start site: forward step i starts at y; backward step i ends at y */
-                    long x = (code > 0) ? y : shift_site(L, y, mu, +1);
-                    for (int e = 0; e < 4; e++) x = shift_site(L, x, e, -disp[e]);
-                    long pos = x;
-                    mat3 A = m_unit(), B = m_unit();
-                    for (int j = 0; j < i; j++) A = m_mul(A, link_step(L, U, &pos, sh[k].step[j]));
-                    (void)link_step(L, U, &pos, code);
-                    for (int j = i + 1; j < sh[k].n; j++) B = m_mul(B, link_step(L, U, &pos, sh[k].step[j]));
-                    double g[8];
-                    if (code > 0) deriv_coef(m_mul(m_mul(u, B), A), g);
-                    else deriv_coef(m_scale(m_mul(m_mul(B, A), m_dag(u)), -1.0), g);
-                    for (int a = 0; a < 8; a++) f[a] += beta * sh[k].w / 3.0 * g[a];
-                }
-            }
-            for (int a = 0; a < 8; a++) F[32 * y + 8 * mu + a] = f[a];
-        }
-    }
+    for (long y = 0; y < V; y++)
+        for (int mu = 0; mu < 4; mu++) gauge_force_link(L, U, sh, ns, beta, y, mu, F + 32 * y + 8 * mu);
+}
+
+/* the force at a list of sites only (all four directions): F[i][mu][8] */
+void orc_gauge_force_sites(const int L[4], const double *U, double beta, double c1, const long *sites, long nsites,
+                           double *F) {
+    init_generators();
+    shape_t sh[64];
+    int ns = make_shapes(c1, sh);
+    #pragma omp parallel for schedule(static)
+    for (long i = 0; i < nsites; i++)
+        for (int mu = 0; mu < 4; mu++) gauge_force_link(L, U, sh, ns, beta, sites[i], mu, F + 32 * i + 8 * mu);
 }
 
 /* ------------------------------------------------------------------ */

@@ -90,6 +90,9 @@ def lib():
         "rmhmc_hamiltonian": ([P, P, P, ctypes.POINTER(Params), DP, DP, DP, P], I),
         "rmhmc_md": ([P, P, P, ctypes.POINTER(Params), ctypes.POINTER(Result), P], I),
         "rmhmc_trajectory": ([P, P, P, ctypes.POINTER(Params), ctypes.POINTER(Result), P, P], I),
+        "rmhmc_set_profiling": ([P, I], I),
+        "rmhmc_get_counters": ([P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(ctypes.c_longlong), DP, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name, None)
@@ -168,6 +171,19 @@ def _links(U):
     if U.dtype == torch.float64:
         return _ptr(U)
     raise ValueError("links must be complex128 [V,4,3,3] (or its float64 view)")
+
+
+def set_profiling(ctx, on=True):
+    ctx.check(lib().rmhmc_set_profiling(ctx.h, int(bool(on))))
+
+
+def counters(ctx, reset=False):
+    """dict(launches, krylov_iters, cg_count, cg_ms) of the context."""
+    a, b, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    d = ctypes.c_double()
+    ctx.check(lib().rmhmc_get_counters(ctx.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d),
+                                       int(bool(reset))))
+    return {"launches": a.value, "krylov_iters": b.value, "cg_count": c.value, "cg_ms": d.value}
 
 
 def set_links(ctx, U, stream=None):
@@ -271,7 +287,7 @@ def gauge_force(ctx, U, beta, c1=0.0, prec=FP64, F=None, stream=None):
     """Returns (F [V,4,8], S, plaquette)."""
     import torch
     if F is None:
-        F = torch.empty((ctx.V, 4, 8), dtype=torch.float64, device=U.device)
+        F = torch.empty((ctx.V, 4, 8), dtype=torch.float64, device="cuda:%d" % ctx.device)
     S = ctypes.c_double()
     pl = ctypes.c_double()
     ctx.check(lib().gauge_force(ctx.h, _links(U), float(beta), float(c1), int(prec), _ptr(F), ctypes.byref(S),
@@ -311,9 +327,10 @@ def link_update(ctx, U, V, eps, reunit=True, out=None, stream=None):
 def make_params(beta=6.0, c1=0.0, mass=None, tau=1.0, nsteps=20, tol_md=1e-10, tol_h=1e-11, fp_tol=1e-10,
                 fp_maxit=50, maxiter=2000, prec=FP64, seed=0, traj_index=0, metropolis=True):
     mass = mass if mass is not None else {"c": 1.0, "alpha": [], "sigma": [], "kappa": 0.0}
-    p = Params(float(beta), float(c1), _mass_struct(mass), float(tau), int(nsteps), float(tol_md), float(tol_h),
+    ms = _mass_struct(mass)
+    p = Params(float(beta), float(c1), ms, float(tau), int(nsteps), float(tol_md), float(tol_h),
                float(fp_tol), int(fp_maxit), int(maxiter), int(prec), int(seed), int(traj_index), int(bool(metropolis)))
-    p._keep = p.mass._keep
+    p._keep = ms._keep   # the struct copy holds raw pointers into these arrays
     return p
 
 
@@ -335,3 +352,72 @@ def rmhmc_trajectory(ctx, U, params, xi=None, P_out=None, stream=None):
     ctx.check(lib().rmhmc_trajectory(ctx.h, _links(U), _ptr(xi), ctypes.byref(params), ctypes.byref(r),
                                      _ptr(P_out), _stream(stream)))
     return r.as_dict()
+
+
+# ------------------------------------------------------------------------------------------------
+# autograd: derivatives with respect to the links in left-multiplication coordinates
+#   U_mu(x) -> exp(i w^a T^a) U_mu(x);  "omega" is a zero tensor [V,4,8] standing for w at w = 0.
+# ------------------------------------------------------------------------------------------------
+def _autograd():
+    import torch
+
+    class LaplacianFn(torch.autograd.Function):
+        """Y = A(U) X.  Backward: dL/dX = A gY (A is symmetric), dL/dw = lap_link_grad(X, gY)."""
+
+        @staticmethod
+        def forward(fctx, omega, X, lat, U, prec):
+            fctx.lat, fctx.U, fctx.prec = lat, U, prec
+            fctx.save_for_backward(X)
+            return lap_apply(lat, U, X, prec=FP64 if X.dtype == torch.float64 else FP32)
+
+        @staticmethod
+        def backward(fctx, gY):
+            (X,) = fctx.saved_tensors
+            gY = gY.contiguous()
+            gX = lap_apply(fctx.lat, fctx.U, gY, prec=FP64 if gY.dtype == torch.float64 else FP32)
+            gw = lap_link_grad(fctx.lat, fctx.U, X.double(), gY.double(), [1.0], prec=fctx.prec)
+            return gw, gX, None, None, None
+
+    class KineticEnergyFn(torch.autograd.Function):
+        """T(U, P) = 1/2 <P, M(U)^{-1} P>.  Backward: dT/dw = -F_K (the hand-written link-adjoint kernel),
+        dT/dP = M^{-1} P.  recompute=True keeps only (U, P) and reruns the Krylov solve in backward."""
+
+        @staticmethod
+        def forward(fctx, omega, P, lat, U, mass, tol, prec, recompute):
+            fctx.lat, fctx.U, fctx.mass, fctx.tol, fctx.prec, fctx.recompute = lat, U, mass, tol, prec, recompute
+            if recompute:
+                _, _, T = kinetic_force(lat, U, P, mass, tol, prec, want_force=False, want_velocity=False)
+                fctx.save_for_backward(P)
+            else:
+                F, Vel, T = kinetic_force(lat, U, P, mass, tol, prec)
+                fctx.save_for_backward(F, Vel)
+            return torch.tensor(T, dtype=torch.float64, device=P.device)
+
+        @staticmethod
+        def backward(fctx, gT):
+            if fctx.recompute:
+                (P,) = fctx.saved_tensors
+                F, Vel, _ = kinetic_force(fctx.lat, fctx.U, P, fctx.mass, fctx.tol, fctx.prec)
+            else:
+                F, Vel = fctx.saved_tensors
+            return -F * gT, Vel * gT, None, None, None, None, None, None
+
+    return LaplacianFn, KineticEnergyFn
+
+
+def laplacian(lat, U, X, omega=None, prec=FP64):
+    """Differentiable Y = A(U) X; omega (zero [V,4,8], requires_grad) receives dL/dw."""
+    import torch
+    LaplacianFn, _ = _autograd()
+    if omega is None:
+        omega = torch.zeros((lat.V, 4, 8), dtype=torch.float64, device=X.device)
+    return LaplacianFn.apply(omega, X, lat, U, prec)
+
+
+def kinetic_energy(lat, U, P, mass, omega=None, tol=1e-12, prec=FP64, recompute=False):
+    """Differentiable T = 1/2 <P, M(U)^{-1} P>; omega.grad = dT/dw = -F_K, P.grad = M^{-1} P."""
+    import torch
+    _, KineticEnergyFn = _autograd()
+    if omega is None:
+        omega = torch.zeros((lat.V, 4, 8), dtype=torch.float64, device=P.device)
+    return KineticEnergyFn.apply(omega, P, lat, U, mass, tol, prec, recompute)

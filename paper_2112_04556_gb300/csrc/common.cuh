@@ -15,7 +15,7 @@
 namespace rm {
 
 constexpr int kBlock = 128;           // threads per block of the site kernels
-constexpr int kRedSlots = 64;         // reduction slots per context (one per concurrent sum)
+constexpr int kRedSlots = 256;        // reduction slots per context (one per concurrent sum)
 
 // ------------------------------------------------------------------------------------------------
 // lattice geometry
@@ -24,14 +24,33 @@ struct Geom {
     int L[4];
     int stride[4];
     int V;
+    // division by L[d] as a multiply-high and shift (Granlund-Montgomery round-up method, exact for
+    // numerators below 2^31 and therefore for every site index): q = (umulhi(mag, n) + n) >> shr
+    unsigned mag[4];
+    int shr[4];
 };
+
+__host__ inline void geom_init_divmod(Geom& g) {
+    for (int d = 0; d < 4; d++) {
+        int l = 0;
+        while ((1u << l) < (unsigned)g.L[d]) l++;
+        const unsigned long long m = ((1ull << 32) * ((1ull << l) - (unsigned long long)g.L[d])) / (unsigned long long)g.L[d] + 1ull;
+        g.mag[d] = (unsigned)(m & 0xffffffffull);
+        g.shr[d] = l;
+    }
+}
+
+__device__ __forceinline__ int fast_div(const Geom& g, int n, int d) {
+    return (int)((__umulhi(g.mag[d], (unsigned)n) + (unsigned)n) >> g.shr[d]);
+}
 
 __device__ __forceinline__ void neighbours(const Geom& g, int s, int fwd[4], int bwd[4]) {
     int r = s;
 #pragma unroll
     for (int d = 0; d < 4; d++) {
-        const int c = r % g.L[d];
-        r /= g.L[d];
+        const int q = fast_div(g, r, d);
+        const int c = r - q * g.L[d];
+        r = q;
         fwd[d] = (c == g.L[d] - 1) ? s - c * g.stride[d] : s + g.stride[d];
         bwd[d] = (c == 0) ? s + (g.L[d] - 1) * g.stride[d] : s - g.stride[d];
     }
@@ -39,7 +58,11 @@ __device__ __forceinline__ void neighbours(const Geom& g, int s, int fwd[4], int
 
 __device__ __forceinline__ void site_coords(const Geom& g, int s, int c[4]) {
 #pragma unroll
-    for (int d = 0; d < 4; d++) { c[d] = s % g.L[d]; s /= g.L[d]; }
+    for (int d = 0; d < 4; d++) {
+        const int q = fast_div(g, s, d);
+        c[d] = s - q * g.L[d];
+        s = q;
+    }
 }
 
 // site reached from coordinates c by n steps along direction d (periodic), without changing c
@@ -230,14 +253,24 @@ struct rmhmc_ctx {
     char* ring = nullptr;
     cudaEvent_t ring_ev[4] = {};
     unsigned ring_idx = 0;
-    // events of the look-behind convergence check of the Krylov loop
+    // events of the look-behind convergence check of the Krylov loop, and the iteration count of the
+    // last run per (precision, shift, tolerance, cap)
     cudaEvent_t kr_ev[2] = {};
+    std::map<std::string, int> kr_pred;
+    // counters: kernels launched; optional timing of the conjugate-gradient stencil launches
+    long long launches = 0;
+    long long krylov_iters = 0;
+    bool prof = false;
+    long long prof_count = 0;
+    double prof_ms = 0.0;
+    cudaEvent_t* prof_ev = nullptr;   // 2 * kProfEvents events, created when profiling is switched on
 };
 
 namespace rm {
 
 constexpr int kPinned = 1 << 16;
 constexpr int kRingSlots = 4;
+constexpr int kProfEvents = 256;
 constexpr size_t kRingBytes = 1 << 20;
 // copy host bytes to device memory asynchronously through the pinned ring
 int upload(rmhmc_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st);
@@ -249,6 +282,8 @@ int import_links(rmhmc_ctx* ctx, const double* U, cudaStream_t st);
 int ensure_links(rmhmc_ctx* ctx, const double* U, cudaStream_t st);
 inline size_t field_elems(const rmhmc_ctx* ctx) { return (size_t)ctx->g.V * 32; }
 inline int site_blocks(const rmhmc_ctx* ctx) { return (ctx->g.V + kBlock - 1) / kBlock; }
+// blocks of the stencil kernels: four lanes per site (one per field component mu)
+inline int lane_blocks(const rmhmc_ctx* ctx) { return (int)(((size_t)ctx->g.V * 4 + kBlock - 1) / kBlock); }
 inline Links64 links64(const rmhmc_ctx* ctx) { return Links64{ctx->u64, ctx->g.V}; }
 inline Links32 links32(const rmhmc_ctx* ctx) { return Links32{ctx->u32a, ctx->u32b, ctx->g.V}; }
 double* red_slot_partials(rmhmc_ctx* ctx, int slot);

@@ -93,7 +93,7 @@ __global__ void k_import_links(const double* __restrict__ U, double2* __restrict
 
 int import_links(rmhmc_ctx* ctx, const double* U, cudaStream_t st) {
     if (((uintptr_t)U) % 16) return set_err(ctx, RMHMC_EINVAL, "links must be 16-byte aligned");
-    k_import_links<<<site_blocks(ctx), kBlock, 0, st>>>(U, ctx->u64, ctx->u32a, ctx->u32b, ctx->g.V);
+    k_import_links<<<site_blocks(ctx), kBlock, 0, st>>>(U, ctx->u64, ctx->u32a, ctx->u32b, ctx->g.V); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     ctx->links_valid = true;
     return RMHMC_OK;
@@ -125,10 +125,11 @@ extern "C" int rmhmc_create(const int dims[4], int device, rmhmc_ctx** out) {
     ctx->g.stride[0] = 1;
     for (int d = 1; d < 4; d++) ctx->g.stride[d] = ctx->g.stride[d - 1] * dims[d - 1];
     ctx->g.V = (int)V;
+    geom_init_divmod(ctx->g);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     ctx->num_sms = sms;
-    ctx->max_blocks = (int)((V + kBlock - 1) / kBlock);
+    ctx->max_blocks = (int)((4 * V + kBlock - 1) / kBlock);   // the stencil kernels use four lanes per site
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&ctx->u64, sizeof(double2) * 36 * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->u32a, sizeof(float4) * 12 * (size_t)V);
@@ -165,6 +166,10 @@ extern "C" int rmhmc_destroy(rmhmc_ctx* ctx) {
     for (int i = 0; i < kRingSlots; i++) if (ctx->ring_ev[i]) cudaEventDestroy(ctx->ring_ev[i]);
     for (int i = 0; i < 2; i++) if (ctx->kr_ev[i]) cudaEventDestroy(ctx->kr_ev[i]);
     for (auto& kv : ctx->bufs) cudaFree(kv.second.p);
+    if (ctx->prof_ev) {
+        for (int i = 0; i < 2 * kProfEvents; i++) cudaEventDestroy(ctx->prof_ev[i]);
+        delete[] ctx->prof_ev;
+    }
     delete ctx;
     return RMHMC_OK;
 }
@@ -175,4 +180,31 @@ extern "C" int rmhmc_set_links(rmhmc_ctx* ctx, const double* U, cudaStream_t str
     if (!ctx || !U) return set_err(ctx, RMHMC_EINVAL, "rmhmc_set_links: null argument");
     ctx->err.clear();
     return import_links(ctx, U, stream);
+}
+
+extern "C" int rmhmc_set_profiling(rmhmc_ctx* ctx, int on) {
+    if (!ctx) return RMHMC_EINVAL;
+    if (on && !ctx->prof_ev) {
+        ctx->prof_ev = new cudaEvent_t[2 * kProfEvents];
+        for (int i = 0; i < 2 * kProfEvents; i++)
+            if (cudaEventCreate(&ctx->prof_ev[i]) != cudaSuccess) return set_err(ctx, RMHMC_ECUDA, "event creation failed");
+    }
+    ctx->prof = on != 0;
+    return RMHMC_OK;
+}
+
+extern "C" int rmhmc_get_counters(rmhmc_ctx* ctx, long long* launches, long long* krylov_iters, long long* cg_count,
+                                  double* cg_ms, int reset) {
+    if (!ctx) return RMHMC_EINVAL;
+    if (launches) *launches = ctx->launches;
+    if (krylov_iters) *krylov_iters = ctx->krylov_iters;
+    if (cg_count) *cg_count = ctx->prof_count;
+    if (cg_ms) *cg_ms = ctx->prof_ms;
+    if (reset) {
+        ctx->launches = 0;
+        ctx->krylov_iters = 0;
+        ctx->prof_count = 0;
+        ctx->prof_ms = 0.0;
+    }
+    return RMHMC_OK;
 }

@@ -1,0 +1,461 @@
+// Sec. 3: the RMHMC trajectory.  Heatbath, Hamiltonian H = 1/2 <P, M^{-1} P> + S[U] (Eq. 5 without
+// the log|M| term), the generalised (implicit) leapfrog of Girolami & Calderhead on SU(3), the float64
+// link update exp(i eps V) U with reunitarisation, and the Metropolis test.
+//
+// One leapfrog step (F = F_G + F_K, V = M^{-1} P):
+//   (1) P' = P + eps/2 F(U, P')                                      fixed point in P'
+//   (2) U' = exp(i eps/2 V(U', P')) exp(i eps/2 V(U, P')) U          fixed point in U'
+//   (3) P'' = P' + eps/2 F(U', P')
+// Iteration rules: (1) starts from the previous step's P'' + eps/2 F (or P + eps/2 F_G(U) on the first
+// step); at iterate Q_i it evaluates F_K and V at (U, Q_i) with one Krylov run and stops when
+// max|Q_{i+1} - Q_i| <= fp_tol, keeping V(U, Q_i).  (2) starts from exp(i eps V) U, evaluates V and F_K
+// at (W_i, P') and stops when max|W_{i+1} - W_i| <= fp_tol, keeping F_K(W_i, P') for (3).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "krylov.cuh"
+#include "ops.cuh"
+#include "philox.cuh"
+
+namespace rm {
+
+constexpr int kSlotMax = 60;
+
+// ------------------------------------------------------------------------------------------------
+// exp(i Q) for Hermitian traceless Q by the Cayley-Hamilton theorem: exp(iQ) = f0 + f1 Q + f2 Q^2.
+// Small Q (c1 = Tr Q^2 / 2 < 1/4): the power series with Q^3 = c1 Q + c0 reducing every power.
+// Otherwise: the closed form of Morningstar & Peardon, Phys. Rev. D 69 (2004) 054501.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void expi_coeffs(double c0, double c1, cplx<double> f[3]) {
+    if (c1 < 0.25) {
+        double a = 1.0, b = 0.0, c = 0.0;   // Q^n = a I + b Q + c Q^2
+        cplx<double> t = cmk(1.0, 0.0);     // i^n / n!
+        f[0] = cmk(0.0, 0.0); f[1] = cmk(0.0, 0.0); f[2] = cmk(0.0, 0.0);
+        for (int n = 0; n < 40; n++) {
+            f[0] = cadd(f[0], cscale(t, a));
+            f[1] = cadd(f[1], cscale(t, b));
+            f[2] = cadd(f[2], cscale(t, c));
+            const double an = c0 * c, bn = a + c1 * c, cn = b;
+            a = an; b = bn; c = cn;
+            t = cscale(cmk(-t.im, t.re), 1.0 / (n + 1));   // t * i / (n+1)
+            if (fabs(t.re) + fabs(t.im) < 1e-18 && n > 2) break;
+        }
+        return;
+    }
+    const bool neg = c0 < 0.0;
+    const double c0p = fabs(c0);
+    const double c0max = 2.0 * pow(c1 / 3.0, 1.5);
+    const double ratio = fmin(1.0, c0p / c0max);
+    const double theta = acos(ratio);
+    const double u = sqrt(c1 / 3.0) * cos(theta / 3.0);
+    const double w = sqrt(c1) * sin(theta / 3.0);
+    const double u2 = u * u, w2 = w * w;
+    const double xi0 = fabs(w) < 0.05 ? 1.0 - w2 / 6.0 * (1.0 - w2 / 20.0 * (1.0 - w2 / 42.0)) : sin(w) / w;
+    const double cw = cos(w);
+    const cplx<double> e2iu = cmk(cos(2.0 * u), sin(2.0 * u));
+    const cplx<double> emiu = cmk(cos(u), -sin(u));
+    const cplx<double> h0 = cadd(cscale(e2iu, u2 - w2), cmul(emiu, cmk(8.0 * u2 * cw, 2.0 * u * (3.0 * u2 + w2) * xi0)));
+    const cplx<double> h1 = csub(cscale(e2iu, 2.0 * u), cmul(emiu, cmk(2.0 * u * cw, -(3.0 * u2 - w2) * xi0)));
+    const cplx<double> h2 = csub(e2iu, cmul(emiu, cmk(cw, 3.0 * u * xi0)));
+    const double den = 1.0 / (9.0 * u2 - w2);
+    f[0] = cscale(h0, den);
+    f[1] = cscale(h1, den);
+    f[2] = cscale(h2, den);
+    if (neg) {   // f_j(-c0) = (-1)^j conj(f_j(c0))
+        f[0] = cconj(f[0]);
+        f[1] = cscale(cconj(f[1]), -1.0);
+        f[2] = cconj(f[2]);
+    }
+}
+
+__device__ __forceinline__ mat3<double> expi(const mat3<double>& Q) {
+    const mat3<double> Q2 = m_mul(Q, Q);
+    const double c1 = 0.5 * re_trace(Q2);
+    const double c0 = re_trace(m_mul(Q, Q2)) / 3.0;
+    cplx<double> f[3];
+    expi_coeffs(c0, c1, f);
+    mat3<double> E;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            cplx<double> v = cadd(cmul(f[1], Q.e[i][j]), cmul(f[2], Q2.e[i][j]));
+            if (i == j) v = cadd(v, f[0]);
+            E.e[i][j] = v;
+        }
+    return E;
+}
+
+// Gram-Schmidt on the first two rows, third row = conj(row0 x row1)
+__device__ __forceinline__ void reunitarise(mat3<double>& U) {
+    double n0 = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) n0 += U.e[0][j].re * U.e[0][j].re + U.e[0][j].im * U.e[0][j].im;
+    n0 = rsqrt(n0);
+#pragma unroll
+    for (int j = 0; j < 3; j++) U.e[0][j] = cscale(U.e[0][j], n0);
+    cplx<double> p = cmk(0.0, 0.0);   // <row0, row1>
+#pragma unroll
+    for (int j = 0; j < 3; j++) p = ccfma(U.e[0][j], U.e[1][j], p);
+#pragma unroll
+    for (int j = 0; j < 3; j++) U.e[1][j] = csub(U.e[1][j], cmul(p, U.e[0][j]));
+    double n1 = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) n1 += U.e[1][j].re * U.e[1][j].re + U.e[1][j].im * U.e[1][j].im;
+    n1 = rsqrt(n1);
+#pragma unroll
+    for (int j = 0; j < 3; j++) U.e[1][j] = cscale(U.e[1][j], n1);
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        U.e[2][j] = cconj(csub(cmul(U.e[0][j1], U.e[1][j2]), cmul(U.e[0][j2], U.e[1][j1])));
+    }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+    if (!(v == v)) v = INFINITY;   // NaN counts as divergence
+    atomicMax((unsigned long long*)addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// Uout = exp(i eps V) Uin per link (canonical layouts).  Optionally: reunitarise, write the internal
+// copies, and record max |Uout - Wold| (max over all entries) into *maxdiff.
+__global__ void __launch_bounds__(kBlock) k_link_update(const double* __restrict__ Uin, const double* __restrict__ V,
+                                                        double eps, int reunit, double* __restrict__ Uout,
+                                                        const double* __restrict__ Wold, double* maxdiff,
+                                                        double2* u64, float4* u32a, float2* u32b, int nsite) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int mu = blockIdx.y;
+    double diff = 0.0;
+    if (s < nsite) {
+        const size_t l = (size_t)s * 4 + mu;
+        double v[8];
+        load8(V + l * 8, v);
+#pragma unroll
+        for (int a = 0; a < 8; a++) v[a] *= eps;
+        const mat3<double> Q = herm_full(coef_to_herm2(v));   // 2 eps V
+        const mat3<double> E = expi(m_scale(Q, 0.5));
+        mat3<double> U;
+        const double2* src = reinterpret_cast<const double2*>(Uin + l * 18);
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) { const double2 z = src[3 * i + j]; U.e[i][j] = cmk(z.x, z.y); }
+        mat3<double> R = m_mul(E, U);
+        if (reunit) reunitarise(R);
+        double2* dst = reinterpret_cast<double2*>(Uout + l * 18);
+        const double2* old = Wold ? reinterpret_cast<const double2*>(Wold + l * 18) : nullptr;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const double2 z = make_double2(R.e[i][j].re, R.e[i][j].im);
+                if (old) {
+                    const double2 o = old[3 * i + j];
+                    diff = fmax(diff, fmax(fabs(z.x - o.x), fabs(z.y - o.y)));
+                }
+                dst[3 * i + j] = z;
+                if (u64) u64[(size_t)(mu * 9 + 3 * i + j) * nsite + s] = z;
+            }
+        if (u32a) {
+            u32a[(size_t)(mu * 3 + 0) * nsite + s] = make_float4(R.e[0][0].re, R.e[0][0].im, R.e[0][1].re, R.e[0][1].im);
+            u32a[(size_t)(mu * 3 + 1) * nsite + s] = make_float4(R.e[0][2].re, R.e[0][2].im, R.e[1][0].re, R.e[1][0].im);
+            u32a[(size_t)(mu * 3 + 2) * nsite + s] = make_float4(R.e[1][1].re, R.e[1][1].im, R.e[1][2].re, R.e[1][2].im);
+#pragma unroll
+            for (int j = 0; j < 3; j++) u32b[(size_t)(mu * 3 + j) * nsite + s] = make_float2(R.e[2][j].re, R.e[2][j].im);
+        }
+    }
+    if (maxdiff) {
+        __shared__ double sh[kBlock / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) diff = fmax(diff, __shfl_down_sync(0xffffffffu, diff, o));
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = diff;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = 0.0;
+            for (int w = 0; w < kBlock / 32; w++) m = fmax(m, sh[w]);
+            atomic_max_nonneg(maxdiff, m);
+        }
+    }
+}
+
+// Qn = P + h (F1 + F2); maxdiff = max |Qn - Qold|; Qn may alias Qold
+__global__ void k_mom_update(const double* __restrict__ P, double h, const double* __restrict__ F1,
+                             const double* __restrict__ F2, const double* Qold, double* Qn, size_t n, double* maxdiff) {
+    double diff = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double q = P[i] + h * (F1[i] + (F2 ? F2[i] : 0.0));
+        if (Qold) diff = fmax(diff, fabs(q - Qold[i]));
+        Qn[i] = q;
+    }
+    if (maxdiff) {
+        __shared__ double sh[kBlock / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) diff = fmax(diff, __shfl_down_sync(0xffffffffu, diff, o));
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = diff;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = 0.0;
+            for (int w = 0; w < kBlock / 32; w++) m = fmax(m, sh[w]);
+            atomic_max_nonneg(maxdiff, m);
+        }
+    }
+}
+
+__global__ void k_gauss_field(double* __restrict__ out, int V, uint64_t seed, uint32_t stream, uint32_t tag) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    double* dst = out + (size_t)s * 32;
+    for (int k = 0; k < 16; k++) {
+        u32x4 c{{(uint32_t)k, (uint32_t)s, stream, tag}};
+        const u32x4 w = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+        const double u0 = u53(w.v[0], w.v[1]), u1 = u53(w.v[2], w.v[3]);
+        const double r = sqrt(-2.0 * log(u0));
+        double sn, cs;
+        sincospi(2.0 * u1, &sn, &cs);
+        dst[2 * k] = r * cs;
+        dst[2 * k + 1] = r * sn;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// host driver
+// ------------------------------------------------------------------------------------------------
+static int link_update_launch(rmhmc_ctx* ctx, const double* Uin, const double* V, double eps, bool reunit, double* Uout,
+                              const double* Wold, double* dmax, bool internal, cudaStream_t st) {
+    const dim3 grid(site_blocks(ctx), 4);
+    k_link_update<<<grid, kBlock, 0, st>>>(Uin, V, eps, reunit ? 1 : 0, Uout, Wold, dmax, internal ? ctx->u64 : nullptr,
+                                           internal ? ctx->u32a : nullptr, internal ? ctx->u32b : nullptr, ctx->g.V); ++ctx->launches;
+    RM_LAUNCH_CHECK(ctx);
+    if (internal) ctx->links_valid = true;
+    return RMHMC_OK;
+}
+
+static int mom_update(rmhmc_ctx* ctx, const double* P, double h, const double* F1, const double* F2, const double* Qold,
+                      double* Qn, double* dmax, cudaStream_t st) {
+    const size_t n = field_elems(ctx);
+    const int grid = (int)std::min<size_t>((n + kBlock - 1) / kBlock, (size_t)ctx->num_sms * 8);
+    k_mom_update<<<grid, kBlock, 0, st>>>(P, h, F1, F2, Qold, Qn, n, dmax); ++ctx->launches;
+    RM_LAUNCH_CHECK(ctx);
+    return RMHMC_OK;
+}
+
+struct MDWork {
+    double *FG, *FK, *V0, *Q, *B, *W, *dmax;
+};
+
+static int md_work(rmhmc_ctx* ctx, MDWork& w) {
+    int status = RMHMC_OK;
+    const size_t fs = field_elems(ctx), ls = (size_t)ctx->g.V * 72;
+    w.FG = (double*)workspace(ctx, "md_fg", sizeof(double) * fs, &status);
+    w.FK = (double*)workspace(ctx, "md_fk", sizeof(double) * fs, &status);
+    w.V0 = (double*)workspace(ctx, "md_v0", sizeof(double) * fs, &status);
+    w.Q = (double*)workspace(ctx, "md_q", sizeof(double) * fs, &status);
+    w.B = (double*)workspace(ctx, "md_b", sizeof(double) * ls, &status);
+    w.W = (double*)workspace(ctx, "md_w", sizeof(double) * ls, &status);
+    w.dmax = (double*)workspace(ctx, "md_dmax", 64, &status);
+    if (!w.FG || !w.FK || !w.V0 || !w.Q || !w.B || !w.W || !w.dmax) return status;
+    return RMHMC_OK;
+}
+
+static int read_max(rmhmc_ctx* ctx, double* dmax, double* out, cudaStream_t st) {
+    RM_TRY(fetch(ctx, dmax, out, 1, st));
+    return RMHMC_OK;
+}
+
+static int check_params(rmhmc_ctx* ctx, const rmhmc_params* p) {
+    if (!p) return set_err(ctx, RMHMC_EINVAL, "null parameters");
+    if (p->nsteps < 1 || !(p->tau > 0.0)) return set_err(ctx, RMHMC_EINVAL, "need tau > 0 and nsteps >= 1");
+    if (!(p->tol_md > 0.0) || !(p->tol_h > 0.0) || !(p->fp_tol > 0.0) || p->fp_maxit < 1 || p->maxiter < 1)
+        return set_err(ctx, RMHMC_EINVAL, "tolerances and iteration caps must be positive");
+    if (p->prec != RMHMC_FP64 && p->prec != RMHMC_MIXED) return set_err(ctx, RMHMC_EINVAL, "bad prec");
+    return RMHMC_OK;
+}
+
+// MD on (U, P) in place.  U canonical device links; the context's links follow U.
+static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, const MassTerm& m, rmhmc_result* r,
+                  cudaStream_t st) {
+    MDWork w;
+    RM_TRY(md_work(ctx, w));
+    const size_t fs = field_elems(ctx), lb = sizeof(double) * (size_t)ctx->g.V * 72;
+    const double eps = p->tau / p->nsteps;
+    const int gprec = p->prec == RMHMC_FP64 ? RMHMC_FP64 : RMHMC_FP32;
+    int fp_p = 0, fp_u = 0, solves = 0;
+    long long kiters = 0;
+    double worst = 0.0;
+    RM_TRY(import_links(ctx, U, st));
+    RM_TRY(gauge_force_launch(ctx, p->beta, p->c1, gprec, w.FG, st));
+    RM_TRY(mom_update(ctx, P, 0.5 * eps, w.FG, nullptr, nullptr, w.Q, nullptr, st));   // Q0 = P + eps/2 F_G
+    for (int step = 0; step < p->nsteps; step++) {
+        // (1) momentum fixed point at fixed U
+        bool conv = false;
+        for (int i = 0; i < p->fp_maxit; i++) {
+            int it = 0;
+            RM_TRY(kinetic_from_krylov(ctx, m, w.Q, p->tol_md, p->maxiter, p->prec, w.FK, w.V0, nullptr, &it, st));
+            solves++;
+            kiters += it;
+            RM_CHECK(ctx, cudaMemsetAsync(w.dmax, 0, sizeof(double), st));
+            RM_TRY(mom_update(ctx, P, 0.5 * eps, w.FG, w.FK, w.Q, w.Q, w.dmax, st));
+            double d = 0.0;
+            RM_TRY(read_max(ctx, w.dmax, &d, st));
+            fp_p++;
+            if (!isfinite(d)) return set_err(ctx, RMHMC_ENAN, "NaN/Inf in the momentum fixed point");
+            if (d <= p->fp_tol) { conv = true; worst = std::max(worst, d); break; }
+        }
+        if (!conv) return set_err(ctx, RMHMC_ENOCONV, "momentum fixed point: no convergence in %d iterations", p->fp_maxit);
+        // (2) link fixed point: B = exp(i eps/2 V0) U ; W = exp(i eps V0) U ; W <- exp(i eps/2 V(W)) B
+        RM_TRY(link_update_launch(ctx, U, w.V0, 0.5 * eps, false, w.B, nullptr, nullptr, false, st));
+        RM_TRY(link_update_launch(ctx, U, w.V0, eps, false, w.W, nullptr, nullptr, true, st));
+        conv = false;
+        for (int i = 0; i < p->fp_maxit; i++) {
+            int it = 0;
+            RM_TRY(kinetic_from_krylov(ctx, m, w.Q, p->tol_md, p->maxiter, p->prec, w.FK, w.V0, nullptr, &it, st));
+            solves++;
+            kiters += it;
+            RM_CHECK(ctx, cudaMemsetAsync(w.dmax, 0, sizeof(double), st));
+            // W_{i+1} into U's buffer (U is no longer needed: B holds exp(i eps/2 V0) U), then swap roles
+            RM_TRY(link_update_launch(ctx, w.B, w.V0, 0.5 * eps, false, U, w.W, w.dmax, true, st));
+            double d = 0.0;
+            RM_TRY(read_max(ctx, w.dmax, &d, st));
+            fp_u++;
+            if (!isfinite(d)) return set_err(ctx, RMHMC_ENAN, "NaN/Inf in the link fixed point");
+            RM_CHECK(ctx, cudaMemcpyAsync(w.W, U, lb, cudaMemcpyDeviceToDevice, st));
+            if (d <= p->fp_tol) { conv = true; worst = std::max(worst, d); break; }
+        }
+        if (!conv) return set_err(ctx, RMHMC_ENOCONV, "link fixed point: no convergence in %d iterations", p->fp_maxit);
+        // reunitarise the accepted links (in place) and refresh the internal copies
+        RM_TRY(link_update_launch(ctx, w.W, w.V0, 0.0, true, U, nullptr, nullptr, true, st));
+        // (3) explicit half step with F_K(W_i, P') kept from the last iteration
+        RM_TRY(gauge_force_launch(ctx, p->beta, p->c1, gprec, w.FG, st));
+        RM_TRY(mom_update(ctx, w.Q, 0.5 * eps, w.FG, w.FK, nullptr, P, nullptr, st));
+        RM_TRY(mom_update(ctx, P, 0.5 * eps, w.FG, w.FK, nullptr, w.Q, nullptr, st));   // next initial guess
+    }
+    if (r) {
+        r->md_solves = solves;
+        r->md_iters = kiters;
+        r->fp_iters_p = fp_p;
+        r->fp_iters_u = fp_u;
+        r->max_fp_change = worst;
+    }
+    (void)fs;
+    return RMHMC_OK;
+}
+
+// T = 1/2 |R(A) P|^2 with every shift at relative residual tol_h (float64 check), S, plaquette
+static int hamiltonian_run(rmhmc_ctx* ctx, const double* U, const double* P, const rmhmc_params* p, const MassTerm& m,
+                           double* H, double* T, double* S, double* plaq, cudaStream_t st) {
+    int status = RMHMC_OK;
+    const size_t fs = field_elems(ctx);
+    RM_TRY(import_links(ctx, U, st));
+    double* Y = (double*)workspace(ctx, "hm_y", sizeof(double) * fs, &status);
+    if (!Y) return status;
+    RM_TRY(rational_apply(ctx, m, P, p->tol_h, p->maxiter, p->prec, Y, nullptr, st));
+    double y2 = 0.0, s = 0.0, pl = 0.0;
+    RM_TRY(norm2_64(ctx, Y, fs, &y2, st));
+    RM_TRY(action_launch(ctx, p->beta, p->c1, &s, &pl, st));
+    const double t = 0.5 * y2;
+    if (!isfinite(t) || !isfinite(s)) return set_err(ctx, RMHMC_ENAN, "NaN/Inf in the Hamiltonian");
+    if (T) *T = t;
+    if (S) *S = s;
+    if (H) *H = t + s;
+    if (plaq) *plaq = pl;
+    return RMHMC_OK;
+}
+
+}  // namespace rm
+
+using namespace rm;
+
+extern "C" int rmhmc_gauss_field(rmhmc_ctx* ctx, double* out, uint64_t seed, uint32_t stream_id, uint32_t tag,
+                                 cudaStream_t stream) {
+    if (!ctx) return RMHMC_EINVAL;
+    ctx->err.clear();
+    if (!out) return set_err(ctx, RMHMC_EINVAL, "rmhmc_gauss_field: null output");
+    k_gauss_field<<<site_blocks(ctx), kBlock, 0, stream>>>(out, ctx->g.V, seed, stream_id, tag); ++ctx->launches;
+    RM_LAUNCH_CHECK(ctx);
+    return RMHMC_OK;
+}
+
+extern "C" int rmhmc_link_update(rmhmc_ctx* ctx, const double* U, const double* V, double eps, int reunit, double* Uout,
+                                 cudaStream_t stream) {
+    if (!ctx) return RMHMC_EINVAL;
+    ctx->err.clear();
+    if (!U || !V || !Uout) return set_err(ctx, RMHMC_EINVAL, "rmhmc_link_update: null argument");
+    return link_update_launch(ctx, U, V, eps, reunit != 0, Uout, nullptr, nullptr, false, stream);
+}
+
+extern "C" int rmhmc_hamiltonian(rmhmc_ctx* ctx, const double* U, const double* P, const rmhmc_params* p, double* H,
+                                 double* T, double* S, cudaStream_t stream) {
+    if (!ctx) return RMHMC_EINVAL;
+    ctx->err.clear();
+    if (!U || !P) return set_err(ctx, RMHMC_EINVAL, "rmhmc_hamiltonian: null argument");
+    RM_TRY(check_params(ctx, p));
+    MassTerm m;
+    RM_TRY(parse_mass(ctx, &p->mass, m));
+    return hamiltonian_run(ctx, U, P, p, m, H, T, S, nullptr, stream);
+}
+
+extern "C" int rmhmc_md(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, rmhmc_result* r,
+                        cudaStream_t stream) {
+    if (!ctx) return RMHMC_EINVAL;
+    ctx->err.clear();
+    if (!U || !P) return set_err(ctx, RMHMC_EINVAL, "rmhmc_md: null argument");
+    RM_TRY(check_params(ctx, p));
+    MassTerm m;
+    RM_TRY(parse_mass(ctx, &p->mass, m));
+    if (r) memset(r, 0, sizeof *r);
+    return md_run(ctx, U, P, p, m, r, stream);
+}
+
+extern "C" int rmhmc_trajectory(rmhmc_ctx* ctx, double* U, const double* xi, const rmhmc_params* p, rmhmc_result* r,
+                                double* P_out, cudaStream_t stream) {
+    if (!ctx) return RMHMC_EINVAL;
+    ctx->err.clear();
+    if (!U) return set_err(ctx, RMHMC_EINVAL, "rmhmc_trajectory: null links");
+    RM_TRY(check_params(ctx, p));
+    MassTerm m;
+    RM_TRY(parse_mass(ctx, &p->mass, m));
+    rmhmc_result res;
+    memset(&res, 0, sizeof res);
+    int status = RMHMC_OK;
+    const size_t fs = field_elems(ctx), lb = sizeof(double) * (size_t)ctx->g.V * 72;
+    double* U0 = (double*)workspace(ctx, "tr_u0", lb, &status);
+    double* P = (double*)workspace(ctx, "tr_p", sizeof(double) * fs, &status);
+    double* X = (double*)workspace(ctx, "tr_xi", sizeof(double) * fs, &status);
+    if (!U0 || !P || !X) return status;
+    RM_CHECK(ctx, cudaMemcpyAsync(U0, U, lb, cudaMemcpyDeviceToDevice, stream));
+    if (xi) {
+        RM_CHECK(ctx, cudaMemcpyAsync(X, xi, sizeof(double) * fs, cudaMemcpyDeviceToDevice, stream));
+    } else {
+        k_gauss_field<<<site_blocks(ctx), kBlock, 0, stream>>>(X, ctx->g.V, p->seed, p->traj_index, 0u); ++ctx->launches;
+        RM_LAUNCH_CHECK(ctx);
+    }
+    auto restore = [&](int code) {
+        cudaMemcpyAsync(U, U0, lb, cudaMemcpyDeviceToDevice, stream);
+        cudaStreamSynchronize(stream);
+        ctx->links_valid = false;
+        return code;
+    };
+    RM_TRY(import_links(ctx, U, stream));
+    int s = heatbath_apply(ctx, m, X, p->tol_h, p->maxiter, p->prec, P, stream);
+    if (s != RMHMC_OK) return restore(s);
+    s = hamiltonian_run(ctx, U, P, p, m, &res.H0, &res.T0, &res.S0, nullptr, stream);
+    if (s != RMHMC_OK) return restore(s);
+    s = md_run(ctx, U, P, p, m, &res, stream);
+    if (s != RMHMC_OK) return restore(s);
+    s = hamiltonian_run(ctx, U, P, p, m, &res.H1, &res.T1, &res.S1, &res.plaq, stream);
+    if (s != RMHMC_OK) return restore(s);
+    res.dH = res.H1 - res.H0;
+    res.u = philox_uniform(p->seed, p->traj_index, 1u);
+    res.accepted = (!p->metropolis || res.dH <= 0.0 || res.u <= exp(-res.dH)) ? 1 : 0;
+    if (P_out) RM_CHECK(ctx, cudaMemcpyAsync(P_out, P, sizeof(double) * fs, cudaMemcpyDeviceToDevice, stream));
+    if (!res.accepted) {
+        RM_CHECK(ctx, cudaMemcpyAsync(U, U0, lb, cudaMemcpyDeviceToDevice, stream));
+        RM_TRY(import_links(ctx, U, stream));
+        RM_TRY(action_launch(ctx, p->beta, p->c1, nullptr, &res.plaq, stream));
+    }
+    RM_CHECK(ctx, cudaStreamSynchronize(stream));
+    if (r) *r = res;
+    return RMHMC_OK;
+}

@@ -1,0 +1,248 @@
+// Kinetic (mass-term) force, Sec. 3 (the force F_M below Eq. 5), and the link-adjoint of the
+// Laplacian stencil it is built from.
+//
+// With T = 1/2 |R(A) P|^2, R(lam) = c + sum_j alpha_j/(lam + sigma_j):
+//   dT = -sum_j alpha_j <Z_j, (dA) X_j>,  X_j = (A+sigma_j)^{-1} P,  Z_j = (A+sigma_j)^{-1} R(A) P,
+// so F_K = -dT/dw = sum_j alpha_j <Z_j, (dA/dw) X_j>.  Only two hops of A contain U = U_nu(y): the
+// forward hop at y and the backward hop at y+nu.  With W1 = U X(y+nu) U^dag, W2 = U Z(y+nu) U^dag,
+//   d<Z, A X>/dw^a = -(1/16) 2i sum_mu Tr(T^a D),   D = [W1, Z(y)] - [X(y), W2] = M - M^dag,
+//   M = W1 Z(y) - X(y) W2,
+// and with K = -i D:  d<Z, A X>/dw^a = (1/16) sum_mu Tr(lambda^a K) = (1/8) sum_mu coef_a(M)
+// where coef_a(M) = Tr(lambda^a (-i)(M - M^dag)/2) (antiherm_coef).
+#include <algorithm>
+
+#include "krylov.cuh"
+#include "ops.cuh"
+#include "stencil.cuh"
+
+namespace rm {
+
+constexpr int kMaxPairs = 24;
+struct PairWeights { double w[kMaxPairs]; };
+
+// one lane per (site y, link direction nu, field component mu); the four component lanes of a link are
+// adjacent and their partial derivatives are summed with two butterfly shuffles
+template <typename T, int LF>
+__global__ void __launch_bounds__(kBlock) k_link_grad(Geom g, typename LinksOf<T>::type U, const T* __restrict__ X,
+                                                       const T* __restrict__ Z, size_t fs, int nf, PairWeights w,
+                                                       double* __restrict__ G) {
+    const int lane = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = lane >> 2, mu = lane & 3;
+    const int nu = blockIdx.y;
+    const bool live = y < g.V;
+    T k[8];
+#pragma unroll
+    for (int a = 0; a < 8; a++) k[a] = T(0);
+    if (live) {
+        int fwd[4], bwd[4];
+        neighbours(g, y, fwd, bwd);
+        const int yp = fwd[nu];
+        const mat3<T> u = LinkLoad<T, LF>::load(U, y, nu);
+        for (int f = 0; f < nf; f++) {
+            const T wf = (T)w.w[f];
+            const T* Xf = X + f * fs;
+            const T* Zf = Z + f * fs;
+            T xb[8];
+            load8(Xf + (size_t)yp * 32 + mu * 8, xb);
+            herm<T> W1 = h_zero<T>();
+            acc_uxud(W1, u, coef_to_herm2(xb));          // 2 W1
+            load8(Zf + (size_t)yp * 32 + mu * 8, xb);
+            herm<T> W2 = h_zero<T>();
+            acc_uxud(W2, u, coef_to_herm2(xb));          // 2 W2
+            load8(Zf + (size_t)y * 32 + mu * 8, xb);
+            const mat3<T> Zy = herm_full(coef_to_herm2(xb));   // 2 Z(y)
+            load8(Xf + (size_t)y * 32 + mu * 8, xb);
+            const mat3<T> Xy = herm_full(coef_to_herm2(xb));   // 2 X(y)
+            mat3<T> M = m_mul(herm_full(W1), Zy);              // 4 W1 Z
+            const mat3<T> M2 = m_mul(Xy, herm_full(W2));       // 4 X W2
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) M.e[i][j] = csub(M.e[i][j], M2.e[i][j]);
+            T kk[8];
+            antiherm_coef(M, kk);                               // 4 coef(M)
+#pragma unroll
+            for (int a = 0; a < 8; a++) k[a] = fma(wf, kk[a], k[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+        k[a] += __shfl_xor_sync(0xffffffffu, k[a], 1);
+        k[a] += __shfl_xor_sync(0xffffffffu, k[a], 2);
+    }
+    if (live && mu == 0) {
+        double* out = G + (size_t)y * 32 + nu * 8;
+        // d<Z,AX>/dw = (1/8) coef(M) and the doubled expansions gave 4 coef(M): scale by 1/32
+#pragma unroll
+        for (int a = 0; a < 8; a++) out[a] = (double)k[a] * (1.0 / 32.0);
+    }
+}
+
+int link_grad_launch(rmhmc_ctx* ctx, int prec, const void* X, const void* Z, int nf, const double* w, double* G,
+                     cudaStream_t st) {
+    if (nf > kMaxPairs) return set_err(ctx, RMHMC_EINVAL, "at most %d field pairs", kMaxPairs);
+    PairWeights pw{};
+    for (int f = 0; f < nf; f++) pw.w[f] = w[f];
+    const dim3 grid(lane_blocks(ctx), 4);
+    if (prec == RMHMC_FP64)
+        k_link_grad<double, 18><<<grid, kBlock, 0, st>>>(ctx->g, links64(ctx), (const double*)X, (const double*)Z,
+                                                         field_elems(ctx), nf, pw, G);
+    else
+        k_link_grad<float, 18><<<grid, kBlock, 0, st>>>(ctx->g, links32(ctx), (const float*)X, (const float*)Z,
+                                                        field_elems(ctx), nf, pw, G);
+    ++ctx->launches;
+    RM_LAUNCH_CHECK(ctx);
+    return RMHMC_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// kinetic pieces from a single Krylov run on P
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+static int kinetic_t(rmhmc_ctx* ctx, const MassTerm& m, const T* P, const double* P64, double tol, int maxiter, double* F,
+                     double* Vel, double* Tkin, int* iters, cudaStream_t st) {
+    const int ns = m.npole();
+    const size_t fs = field_elems(ctx);
+    int status = RMHMC_OK;
+    if (ns == 0) {
+        // M = c^{-2}: V = c^2 P, F_K = 0, T = c^2 |P|^2 / 2
+        if (F) RM_CHECK(ctx, cudaMemsetAsync(F, 0, sizeof(double) * fs, st));
+        if (Vel) RM_TRY(axpby64(ctx, m.c * m.c, P64, 0.0, nullptr, Vel, fs, st));
+        if (Tkin) {
+            double n2 = 0.0;
+            RM_TRY(norm2_64(ctx, P64, fs, &n2, st));
+            *Tkin = 0.5 * m.c * m.c * n2;
+        }
+        if (iters) *iters = 0;
+        return RMHMC_OK;
+    }
+    const double s0 = *std::min_element(m.sigma.begin(), m.sigma.end());
+    KrylovResult kr;
+    RM_TRY(krylov_run<T>(ctx, P, s0, tol, maxiter, kr, st));
+    if (kr.status == 2) return set_err(ctx, RMHMC_ENOCONV, "kinetic force: Krylov run hit its cap (%d)", kr.n);
+    if (iters) *iters = kr.n;
+    Tridiag tri;
+    tri.build(kr);
+    const int n = tri.n;
+    // Galerkin coefficient vectors: y_j = (T+D_j)^{-1} e1|b|, g = R(T) e1|b|, z_j = (T+D_j)^{-1} g, v = R(T) g
+    std::vector<double> e1(n, 0.0), g(n, 0.0), v(n, 0.0);
+    if (n > 0) e1[0] = tri.bnorm;
+    std::vector<std::vector<double>> ys(ns), zs(ns);
+    for (int j = 0; j < ns; j++) tri.solve(m.sigma[j] - s0, e1, ys[j]);
+    for (int k = 0; k < n; k++) {
+        g[k] = m.c * e1[k];
+        for (int j = 0; j < ns; j++) g[k] += m.alpha[j] * ys[j][k];
+    }
+    for (int j = 0; j < ns; j++) tri.solve(m.sigma[j] - s0, g, zs[j]);
+    for (int k = 0; k < n; k++) {
+        v[k] = m.c * g[k];
+        for (int j = 0; j < ns; j++) v[k] += m.alpha[j] * zs[j][k];
+    }
+    if (Tkin) {
+        // T = 1/2 |R P|^2 from the explicitly formed R P (float64 sum), not from |g|, which would
+        // assume exactly orthonormal Lanczos vectors
+        double* Y = (double*)workspace(ctx, "kf_y", sizeof(double) * fs, &status);
+        if (!Y) return status;
+        CombineSpec spec;
+        spec.n = n;
+        spec.M = 1;
+        spec.coef.assign(n, 0.0);
+        tri.to_basis(g, spec.coef.data());
+        double* o[1] = {Y};
+        RM_TRY((krylov_combine<T, double>(ctx, spec, o, st)));
+        double y2 = 0.0;
+        RM_TRY(norm2_64(ctx, Y, fs, &y2, st));
+        *Tkin = 0.5 * y2;
+    }
+    if (Vel) {
+        CombineSpec spec;
+        spec.n = n;
+        spec.M = 1;
+        spec.coef.assign(n, 0.0);
+        tri.to_basis(v, spec.coef.data());
+        double* o[1] = {Vel};
+        RM_TRY((krylov_combine<T, double>(ctx, spec, o, st)));
+    }
+    if (F) {
+        T* XZ = (T*)workspace(ctx, sizeof(T) == 4 ? "kf_xz32" : "kf_xz64", sizeof(T) * fs * 2 * ns, &status);
+        if (!XZ) return status;
+        CombineSpec spec;
+        spec.n = n;
+        spec.M = 2 * ns;
+        spec.coef.assign((size_t)2 * ns * n, 0.0);
+        std::vector<T*> outs(2 * ns);
+        for (int j = 0; j < ns; j++) {
+            tri.to_basis(ys[j], spec.coef.data() + (size_t)j * n);
+            tri.to_basis(zs[j], spec.coef.data() + (size_t)(ns + j) * n);
+            outs[j] = XZ + (size_t)j * fs;
+            outs[ns + j] = XZ + (size_t)(ns + j) * fs;
+        }
+        RM_TRY((krylov_combine<T, T>(ctx, spec, outs.data(), st)));
+        RM_TRY(link_grad_launch(ctx, sizeof(T) == 8 ? RMHMC_FP64 : RMHMC_FP32, XZ, XZ + (size_t)ns * fs, ns,
+                                m.alpha.data(), F, st));
+    }
+    return RMHMC_OK;
+}
+
+int kinetic_from_krylov(rmhmc_ctx* ctx, const MassTerm& m, const double* P, double tol, int maxiter, int prec,
+                        double* F, double* Vel, double* T, int* iters, cudaStream_t st) {
+    if (prec == RMHMC_FP64) return kinetic_t<double>(ctx, m, P, P, tol, maxiter, F, Vel, T, iters, st);
+    int status = RMHMC_OK;
+    const size_t fs = field_elems(ctx);
+    float* P32 = (float*)workspace(ctx, "kf_p32", sizeof(float) * fs, &status);
+    if (!P32) return status;
+    RM_TRY(to_float(ctx, P, P32, fs, st));
+    return kinetic_t<float>(ctx, m, P32, P, tol, maxiter, F, Vel, T, iters, st);
+}
+
+}  // namespace rm
+
+using namespace rm;
+
+extern "C" int lap_link_grad(rmhmc_ctx* ctx, const double* U, const double* X, const double* Z, int nfield,
+                             const double* w, int prec, double* G, cudaStream_t stream) {
+    if (!ctx) return RMHMC_EINVAL;
+    ctx->err.clear();
+    if (!X || !Z || !G || (nfield > 0 && !w)) return set_err(ctx, RMHMC_EINVAL, "lap_link_grad: null argument");
+    if (nfield < 0 || nfield > kMaxPairs) return set_err(ctx, RMHMC_EINVAL, "lap_link_grad: nfield in [0, %d]", kMaxPairs);
+    if (prec != RMHMC_FP64 && prec != RMHMC_FP32) return set_err(ctx, RMHMC_EINVAL, "lap_link_grad: bad prec");
+    RM_TRY(ensure_links(ctx, U, stream));
+    const size_t fs = field_elems(ctx);
+    if (nfield == 0) {
+        RM_CHECK(ctx, cudaMemsetAsync(G, 0, sizeof(double) * fs, stream));
+        return RMHMC_OK;
+    }
+    if (prec == RMHMC_FP64) return link_grad_launch(ctx, prec, X, Z, nfield, w, G, stream);
+    int status = RMHMC_OK;
+    float* buf = (float*)workspace(ctx, "lg_xz32", sizeof(float) * fs * 2 * nfield, &status);
+    if (!buf) return status;
+    RM_TRY(to_float(ctx, X, buf, fs * nfield, stream));
+    RM_TRY(to_float(ctx, Z, buf + fs * nfield, fs * nfield, stream));
+    return link_grad_launch(ctx, prec, buf, buf + fs * nfield, nfield, w, G, stream);
+}
+
+extern "C" int kinetic_force(rmhmc_ctx* ctx, const double* U, const double* P, const rmhmc_mass* mass, double tol,
+                             int prec, double* F, double* Vout, double* T, cudaStream_t stream) {
+    if (!ctx) return RMHMC_EINVAL;
+    ctx->err.clear();
+    if (!P) return set_err(ctx, RMHMC_EINVAL, "kinetic_force: null momenta");
+    if (!(tol > 0.0)) return set_err(ctx, RMHMC_EINVAL, "kinetic_force: tol must be > 0");
+    if (prec != RMHMC_FP64 && prec != RMHMC_MIXED) return set_err(ctx, RMHMC_EINVAL, "kinetic_force: bad prec");
+    MassTerm m;
+    RM_TRY(parse_mass(ctx, mass, m));
+    RM_TRY(ensure_links(ctx, U, stream));
+    return kinetic_from_krylov(ctx, m, P, tol, 1000, prec, F, Vout, T, nullptr, stream);
+}
+
+extern "C" int rmhmc_heatbath(rmhmc_ctx* ctx, const double* U, const double* xi, const rmhmc_mass* mass, double tol,
+                              int prec, double* P, cudaStream_t stream) {
+    if (!ctx) return RMHMC_EINVAL;
+    ctx->err.clear();
+    if (!xi || !P) return set_err(ctx, RMHMC_EINVAL, "rmhmc_heatbath: null field");
+    if (!(tol > 0.0)) return set_err(ctx, RMHMC_EINVAL, "rmhmc_heatbath: tol must be > 0");
+    if (prec != RMHMC_FP64 && prec != RMHMC_MIXED) return set_err(ctx, RMHMC_EINVAL, "rmhmc_heatbath: bad prec");
+    MassTerm m;
+    RM_TRY(parse_mass(ctx, mass, m));
+    RM_TRY(ensure_links(ctx, U, stream));
+    return heatbath_apply(ctx, m, xi, tol, 1000, prec, P, stream);
+}

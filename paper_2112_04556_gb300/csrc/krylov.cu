@@ -18,21 +18,36 @@ constexpr int kMaxCombine = 32;                                                /
 // ------------------------------------------------------------------------------------------------
 // elementwise field kernels (one thread per site, 32 reals)
 // ------------------------------------------------------------------------------------------------
+// flat vector access: element i of a field as the i-th float4 (float) or double2 (double)
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+    using type = float4;
+    static constexpr int n = 4;
+    __device__ __forceinline__ static void get(const type& v, float* x) { x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w; }
+    __device__ __forceinline__ static type make(const float* x) { return make_float4(x[0], x[1], x[2], x[3]); }
+};
+template <> struct Vec<double> {
+    using type = double2;
+    static constexpr int n = 2;
+    __device__ __forceinline__ static void get(const type& v, double* x) { x[0] = v.x; x[1] = v.y; }
+    __device__ __forceinline__ static type make(const double* x) { return make_double2(x[0], x[1]); }
+};
+
+// r_0 = b, rho_0 = |b|^2 (one vector element per thread, coalesced)
 template <typename T>
-__global__ void k_cg_start(const T* __restrict__ b, T* __restrict__ r0, int V, int* flags, double* rho,
-                           double* partials, unsigned* counter) {
+__global__ void __launch_bounds__(kBlock) k_cg_start(const T* __restrict__ b, T* __restrict__ r0, size_t nvec, int* flags,
+                                                     double* rho, double* partials, unsigned* counter) {
     __shared__ double sh[kBlock / 32];
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    using VT = Vec<T>;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     double acc = 0.0;
-    if (s < V) {
+    if (i < nvec) {
+        const typename VT::type v = reinterpret_cast<const typename VT::type*>(b)[i];
+        reinterpret_cast<typename VT::type*>(r0)[i] = v;
+        T x[VT::n];
+        VT::get(v, x);
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            T x[8];
-            load8(b + (size_t)s * 32 + mu * 8, x);
-            store8(r0 + (size_t)s * 32 + mu * 8, x);
-#pragma unroll
-            for (int k = 0; k < 8; k++) acc += (double)x[k] * (double)x[k];
-        }
+        for (int k = 0; k < VT::n; k++) acc += (double)x[k] * (double)x[k];
     }
     double v[1] = {acc};
     block_sum<1>(v, sh);
@@ -46,38 +61,43 @@ __global__ void k_cg_start(const T* __restrict__ b, T* __restrict__ r0, int V, i
     }
 }
 
-// q = (A + sigma0) p_k with p_k = r_k + beta_{k-1} p_{k-1} formed on the fly; gamma_k = <p_k, q>
+// CG without the search direction: q_k = (A + sigma0) p_k is carried as q_k = (A + sigma0) r_k + beta_{k-1} q_{k-1}
+// (p_k = r_k + beta_{k-1} p_{k-1}), so the stencil reads only r_k; gamma_k = <p_k, A p_k> = <r_k, q_k> by
+// A-conjugacy of the directions, alpha_k = rho_k / gamma_k.  q is updated in place at the lane's own site.
 template <typename T, int LF>
-__global__ void __launch_bounds__(kBlock) k_cg_A(Geom g, typename LinksOf<T>::type U, const T* __restrict__ r,
-                                                  const T* __restrict__ pold, T* __restrict__ pnew, T* __restrict__ q,
-                                                  T diag, int k, const int* __restrict__ flags, double* vals, int maxit,
-                                                  double* partials, unsigned* counter) {
+__global__ void __launch_bounds__(kBlock) k_cg_A(Geom g, typename LinksOf<T>::type U, const T* __restrict__ R, size_t fs,
+                                                  T* __restrict__ q, T diag, const int* __restrict__ flags,
+                                                  double* vals, int maxit, double* partials, unsigned* counter) {
     __shared__ double sh[kBlock / 32];
     if (flags[0]) return;
+    const int k = flags[1];
+    const T* r = R + (size_t)k * fs;
     const double* rho = vals;
     double* gamma = vals + (maxit + 1);
     double* alpha = gamma + maxit;
     const double* beta = alpha + maxit;
     const T b = k > 0 ? (T)beta[k - 1] : T(0);
-    const SrcAxpy<T> src{r, k > 0 ? pold : nullptr, b};
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = lane >> 2, mu = lane & 3;
     T dot = T(0);
     if (s < g.V) {
-        herm<T> acc[4];
-        hop_sum4<T, LF>(g, U, s, src, acc);
+        herm<T> acc;
+        hop_sum1<T, LF>(g, U, s, mu, SrcField<T>{r}, acc);
+        T h[8], x[8], y[8];
+        herm2_to_coef(acc, h);
+        load8(r + (size_t)s * 32 + mu * 8, x);
+        T* qs = q + (size_t)s * 32 + mu * 8;
+        if (k > 0) {
+            load8(qs, y);
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            T h[8], x[8], y[8];
-            herm2_to_coef(acc[mu], h);
-            src(s, mu, x);
+            for (int a = 0; a < 8; a++) y[a] = fma(b, y[a], fma(T(-0.0625), h[a], diag * x[a]));
+        } else {
 #pragma unroll
-            for (int a = 0; a < 8; a++) {
-                y[a] = fma(T(-0.0625), h[a], diag * x[a]);
-                dot = fma(x[a], y[a], dot);
-            }
-            store8(pnew + (size_t)s * 32 + mu * 8, x);
-            store8(q + (size_t)s * 32 + mu * 8, y);
+            for (int a = 0; a < 8; a++) y[a] = fma(T(-0.0625), h[a], diag * x[a]);
         }
+#pragma unroll
+        for (int a = 0; a < 8; a++) dot = fma(x[a], y[a], dot);
+        store8(qs, y);
     }
     double v[1];
     if (sizeof(T) == 4) {
@@ -101,33 +121,32 @@ __global__ void __launch_bounds__(kBlock) k_cg_A(Geom g, typename LinksOf<T>::ty
     }
 }
 
-// r_{k+1} = r_k - alpha_k q ; rho_{k+1} = |r_{k+1}|^2 ; convergence flags
+// r_{k+1} = r_k - alpha_k q_k ; rho_{k+1} = |r_{k+1}|^2 ; beta_k ; convergence flags; k advances
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_cg_B(const T* __restrict__ r, T* __restrict__ rn, const T* __restrict__ q,
-                                                  int V, int k, int* flags, double* vals, int maxit, double tol2,
-                                                  double* partials, unsigned* counter) {
+__global__ void __launch_bounds__(kBlock) k_cg_B(T* __restrict__ R, size_t fs, const T* __restrict__ q, size_t nvec,
+                                                  int* flags, double* vals, int maxit, double tol2, double* partials,
+                                                  unsigned* counter) {
     __shared__ double sh[kBlock / 32];
     if (flags[0]) return;
+    const int k = flags[1];
     double* rho = vals;
     const double* gamma = vals + (maxit + 1);
     const double* alpha = gamma + maxit;
     double* beta = (double*)(alpha + maxit);
+    using VT = Vec<T>;
     const T a = (T)alpha[k];
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     T dot = T(0);
-    if (s < V) {
+    if (i < nvec) {
+        T x[VT::n], y[VT::n];
+        VT::get(reinterpret_cast<const typename VT::type*>(R + (size_t)k * fs)[i], x);
+        VT::get(reinterpret_cast<const typename VT::type*>(q)[i], y);
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            T x[8], y[8];
-            load8(r + (size_t)s * 32 + mu * 8, x);
-            load8(q + (size_t)s * 32 + mu * 8, y);
-#pragma unroll
-            for (int c = 0; c < 8; c++) {
-                x[c] = fma(-a, y[c], x[c]);
-                dot = fma(x[c], x[c], dot);
-            }
-            store8(rn + (size_t)s * 32 + mu * 8, x);
+        for (int c = 0; c < VT::n; c++) {
+            x[c] = fma(-a, y[c], x[c]);
+            dot = fma(x[c], x[c], dot);
         }
+        reinterpret_cast<typename VT::type*>(R + (size_t)(k + 1) * fs)[i] = VT::make(x);
     }
     double v[1];
     if (sizeof(T) == 4) {
@@ -159,19 +178,20 @@ __global__ void __launch_bounds__(kBlock) k_cg_B(const T* __restrict__ r, T* __r
     }
 }
 
-// out[m] = sum_k coef[m][k] basis_k, two reals per thread; coefficients staged through shared memory
+// out[m] = sum_k coef[m][k] basis_k; one real per thread (coalesced), coefficients staged through shared
+// memory, eight basis vectors in flight per step
 template <typename T, typename TO>
 struct OutPtrs { TO* p[kMaxCombine]; };
 
 template <typename T, typename TO>
 __global__ void __launch_bounds__(kBlock) k_combine(const T* __restrict__ R, size_t fs, int n, const double* __restrict__ coef,
-                                                     int M, OutPtrs<T, TO> outs, size_t npair) {
-    constexpr int KC = 64;
+                                                     int M, OutPtrs<T, TO> outs) {
+    constexpr int KC = 64, UN = 8;
     __shared__ T cs[kMaxCombine * KC];
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    T acc0[kMaxCombine], acc1[kMaxCombine];
+    T acc[kMaxCombine];
 #pragma unroll
-    for (int m = 0; m < kMaxCombine; m++) { acc0[m] = T(0); acc1[m] = T(0); }
+    for (int m = 0; m < kMaxCombine; m++) acc[m] = T(0);
     for (int k0 = 0; k0 < n; k0 += KC) {
         const int kc = min(KC, n - k0);
         __syncthreads();
@@ -180,33 +200,30 @@ __global__ void __launch_bounds__(kBlock) k_combine(const T* __restrict__ R, siz
             cs[m * KC + kk] = (T)coef[(size_t)m * n + k0 + kk];
         }
         __syncthreads();
-        if (i < npair) {
-            for (int kk = 0; kk < kc; kk++) {
-                T x0, x1;
-                if (sizeof(T) == 4) {
-                    const float2 v = __ldg(reinterpret_cast<const float2*>(R + (size_t)(k0 + kk) * fs) + i);
-                    x0 = (T)v.x; x1 = (T)v.y;
-                } else {
-                    const double2 v = __ldg(reinterpret_cast<const double2*>(R + (size_t)(k0 + kk) * fs) + i);
-                    x0 = (T)v.x; x1 = (T)v.y;
-                }
+        if (i < fs) {
+            int kk = 0;
+            for (; kk + UN <= kc; kk += UN) {
+                T x[UN];
+#pragma unroll
+                for (int u = 0; u < UN; u++) x[u] = __ldg(R + (size_t)(k0 + kk + u) * fs + i);
+#pragma unroll
+                for (int u = 0; u < UN; u++)
+#pragma unroll
+                    for (int m = 0; m < kMaxCombine; m++)
+                        if (m < M) acc[m] = fma(cs[m * KC + kk + u], x[u], acc[m]);
+            }
+            for (; kk < kc; kk++) {
+                const T x = __ldg(R + (size_t)(k0 + kk) * fs + i);
 #pragma unroll
                 for (int m = 0; m < kMaxCombine; m++)
-                    if (m < M) {
-                        const T c = cs[m * KC + kk];
-                        acc0[m] = fma(c, x0, acc0[m]);
-                        acc1[m] = fma(c, x1, acc1[m]);
-                    }
+                    if (m < M) acc[m] = fma(cs[m * KC + kk], x, acc[m]);
             }
         }
     }
-    if (i < npair) {
+    if (i < fs) {
 #pragma unroll
         for (int m = 0; m < kMaxCombine; m++)
-            if (m < M) {
-                outs.p[m][2 * i] = (TO)acc0[m];
-                outs.p[m][2 * i + 1] = (TO)acc1[m];
-            }
+            if (m < M) outs.p[m][i] = (TO)acc[m];
     }
 }
 
@@ -219,24 +236,22 @@ __global__ void __launch_bounds__(kBlock) k_resid64(Geom g, Links64 U, const dou
     const int f = blockIdx.y;
     const double* xf = x + f * fs;
     const double diag = 0.5 + sig[f];
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = lane >> 2, mu = lane & 3;
     double nrm = 0.0;
     if (s < g.V) {
-        herm<double> acc[4];
-        hop_sum4<double, LF>(g, U, s, SrcField<double>{xf}, acc);
+        herm<double> acc;
+        hop_sum1<double, LF>(g, U, s, mu, SrcField<double>{xf}, acc);
+        double h[8], xx[8], bb[8], y[8];
+        herm2_to_coef(acc, h);
+        load8(xf + (size_t)s * 32 + mu * 8, xx);
+        load8(b + (size_t)s * 32 + mu * 8, bb);
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            double h[8], xx[8], bb[8], y[8];
-            herm2_to_coef(acc[mu], h);
-            load8(xf + (size_t)s * 32 + mu * 8, xx);
-            load8(b + (size_t)s * 32 + mu * 8, bb);
-#pragma unroll
-            for (int a = 0; a < 8; a++) {
-                y[a] = bb[a] - (diag * xx[a] - 0.0625 * h[a]);
-                nrm = fma(y[a], y[a], nrm);
-            }
-            if (r) store8(r + f * fs + (size_t)s * 32 + mu * 8, y);
+        for (int a = 0; a < 8; a++) {
+            y[a] = bb[a] - (diag * xx[a] - 0.0625 * h[a]);
+            nrm = fma(y[a], y[a], nrm);
         }
+        if (r) store8(r + f * fs + (size_t)s * 32 + mu * 8, y);
     }
     double v[1] = {nrm};
     block_sum<1>(v, sh);
@@ -274,24 +289,24 @@ static int elem_grid(const rmhmc_ctx* ctx, size_t n) {
 }
 
 int to_float(rmhmc_ctx* ctx, const double* in, float* out, size_t n, cudaStream_t st) {
-    k_to_float<<<elem_grid(ctx, n), kBlock, 0, st>>>(in, out, n);
+    k_to_float<<<elem_grid(ctx, n), kBlock, 0, st>>>(in, out, n); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     return RMHMC_OK;
 }
 int add_float_to_double(rmhmc_ctx* ctx, const float* in, double* out, size_t n, cudaStream_t st) {
-    k_add_f2d<<<elem_grid(ctx, n), kBlock, 0, st>>>(in, out, n);
+    k_add_f2d<<<elem_grid(ctx, n), kBlock, 0, st>>>(in, out, n); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     return RMHMC_OK;
 }
 int axpby64(rmhmc_ctx* ctx, double a, const double* x, double b, const double* y, double* out, size_t n, cudaStream_t st) {
-    k_axpby64<<<elem_grid(ctx, n), kBlock, 0, st>>>(a, x, b, y, out, n);
+    k_axpby64<<<elem_grid(ctx, n), kBlock, 0, st>>>(a, x, b, y, out, n); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     return RMHMC_OK;
 }
 int norm2_64(rmhmc_ctx* ctx, const double* x, size_t n, double* out, cudaStream_t st) {
     const int grid = std::min(elem_grid(ctx, n), ctx->max_blocks);
     k_norm2_64<<<grid, kBlock, 0, st>>>(x, n, red_slot_partials(ctx, kSlotNorm), red_slot_counter(ctx, kSlotNorm),
-                                        red_slot_out(ctx, kSlotNorm));
+                                        red_slot_out(ctx, kSlotNorm)); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     return fetch(ctx, red_slot_out(ctx, kSlotNorm), out, 1, st);
 }
@@ -340,9 +355,10 @@ void Tridiag::to_basis(const std::vector<double>& y, double* row) const {
 // ------------------------------------------------------------------------------------------------
 struct KWork {
     void* basis = nullptr;
-    void *p0 = nullptr, *p1 = nullptr, *q = nullptr;
+    void* q = nullptr;
     int* flags = nullptr;
     double* vals = nullptr;
+    double* coef = nullptr;
     int maxit = 0;
 };
 // the stored basis holds at most kBasisCap residuals: longer runs stop there and the caller's
@@ -356,11 +372,9 @@ static int krylov_workspace(rmhmc_ctx* ctx, int maxit, KWork& w) {
     const bool f32 = sizeof(T) == 4;
     w.basis = workspace(ctx, f32 ? "kr_basis32" : "kr_basis64", fb * (size_t)(maxit + 1), &status);
     if (!w.basis) return status;
-    w.p0 = workspace(ctx, f32 ? "kr_p0_32" : "kr_p0_64", fb, &status);
-    w.p1 = workspace(ctx, f32 ? "kr_p1_32" : "kr_p1_64", fb, &status);
     w.q = workspace(ctx, f32 ? "kr_q32" : "kr_q64", fb, &status);
-    void* sc = workspace(ctx, "kr_scal", 64 + sizeof(double) * 4 * (size_t)(maxit + 2), &status);
-    if (!w.p0 || !w.p1 || !w.q || !sc) return status;
+    void* sc = workspace(ctx, "kr_scal", 64 + sizeof(double) * 4 * (size_t)(kBasisCap + 2), &status);
+    if (!w.q || !sc) return status;
     w.flags = (int*)sc;
     w.vals = (double*)((char*)sc + 64);
     w.maxit = maxit;
@@ -381,62 +395,80 @@ int krylov_run(rmhmc_ctx* ctx, const T* b, double sigma0, double tol, int maxit,
     KWork w;
     RM_TRY(krylov_workspace<T>(ctx, maxit, w));
     const size_t fs = field_elems(ctx);
+    const size_t nvec = fs / Vec<T>::n;
     T* R = (T*)w.basis;
-    const int nb = site_blocks(ctx);
-    k_cg_start<T><<<nb, kBlock, 0, st>>>(b, R, ctx->g.V, w.flags, w.vals, red_slot_partials(ctx, kSlotRho),
-                                         red_slot_counter(ctx, kSlotRho));
+    const int nb = (int)((nvec + kBlock - 1) / kBlock);
+    const int nl = lane_blocks(ctx);
+    k_cg_start<T><<<nb, kBlock, 0, st>>>(b, R, nvec, w.flags, w.vals, red_slot_partials(ctx, kSlotRho),
+                                         red_slot_counter(ctx, kSlotRho)); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     typename LinksOf<T>::type U;
     if constexpr (sizeof(T) == 8) U = links64(ctx); else U = links32(ctx);
     const T diag = (T)(0.5 + sigma0);
     const double tol2 = tol * tol;
-    // pinned flag slots for the look-behind convergence check
+    // iteration count of the previous run of the same operator and tolerance: the first chunk of launches
+    // covers it, so a converged run usually stops after one host check
+    char key[96];
+    snprintf(key, sizeof key, "%d:%.17g:%.17g:%d", (int)sizeof(T), sigma0, tol, maxit);
+    int& pred = ctx->kr_pred[key];
     int* hflags = (int*)(ctx->h_pinned + kPinned - 16);
     cudaEvent_t* ev = ctx->kr_ev;
-    int chunk = 0;
+    int launched = 0, chunk = 0;
     bool stop = false;
-    for (int k0 = 0; k0 < maxit && !stop; k0 += kCheckChunk, chunk++) {
-        const int k1 = std::min(maxit, k0 + kCheckChunk);
-        for (int k = k0; k < k1; k++) {
-            const T* r = R + (size_t)k * fs;
-            T* rn = R + (size_t)(k + 1) * fs;
-            T* pold = (T*)((k & 1) ? w.p0 : w.p1);
-            T* pnew = (T*)((k & 1) ? w.p1 : w.p0);
-            if (ctx->g.V > 0) {
-                // the stencil kernel is instantiated per link format; 18-real links throughout the solver
-                k_cg_A<T, 18><<<nb, kBlock, 0, st>>>(ctx->g, U, r, pold, pnew, (T*)w.q, diag, k, w.flags, w.vals, maxit,
-                                                     red_slot_partials(ctx, kSlotGamma), red_slot_counter(ctx, kSlotGamma));
-                k_cg_B<T><<<nb, kBlock, 0, st>>>(r, rn, (const T*)w.q, ctx->g.V, k, w.flags, w.vals, maxit, tol2,
-                                                 red_slot_partials(ctx, kSlotRho), red_slot_counter(ctx, kSlotRho));
-            }
+    while (launched < maxit && !stop) {
+        const int len = chunk == 0 ? (pred > 0 ? pred : kCheckChunk) : kCheckChunk / 2;
+        const int k1 = std::min(maxit, launched + len);
+        for (int k = launched; k < k1; k++) {
+            const bool timed = ctx->prof && k < kProfEvents;
+            if (timed) RM_CHECK(ctx, cudaEventRecord(ctx->prof_ev[2 * k], st));
+            // the solver streams 18-real links
+            k_cg_A<T, 18><<<nl, kBlock, 0, st>>>(ctx->g, U, R, fs, (T*)w.q, diag, w.flags, w.vals, maxit,
+                                                 red_slot_partials(ctx, kSlotGamma), red_slot_counter(ctx, kSlotGamma)); ++ctx->launches;
+            if (timed) RM_CHECK(ctx, cudaEventRecord(ctx->prof_ev[2 * k + 1], st));
+            k_cg_B<T><<<nb, kBlock, 0, st>>>(R, fs, (const T*)w.q, nvec, w.flags, w.vals, maxit, tol2,
+                                             red_slot_partials(ctx, kSlotRho), red_slot_counter(ctx, kSlotRho)); ++ctx->launches;
         }
+        launched = k1;
         RM_LAUNCH_CHECK(ctx);
         const int slot = chunk & 1;
         RM_CHECK(ctx, cudaMemcpyAsync(hflags + 2 * slot, w.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         RM_CHECK(ctx, cudaEventRecord(ev[slot], st));
-        // inspect the previous chunk's flags while this chunk runs
-        if (chunk > 0) {
+        if (chunk == 0) {
+            // the predicted length: check at once
+            RM_CHECK(ctx, cudaEventSynchronize(ev[slot]));
+            if (hflags[2 * slot] != 0) stop = true;
+        } else if (chunk > 1) {
+            // inspect the previous chunk's flags while this chunk runs
             RM_CHECK(ctx, cudaEventSynchronize(ev[slot ^ 1]));
             if (hflags[2 * (slot ^ 1)] != 0) stop = true;
         }
+        chunk++;
     }
     RM_CHECK(ctx, cudaMemcpyAsync(hflags, w.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     RM_CHECK(ctx, cudaStreamSynchronize(st));
     out.status = hflags[0];
     out.n = hflags[1];
+    pred = out.n;
+    ctx->krylov_iters += out.n;
+    if (ctx->prof) {
+        // durations of the stencil launches that did work (iterations 0 .. n-1)
+        for (int k = 0; k < std::min(out.n, kProfEvents); k++) {
+            float ms = 0.f;
+            RM_CHECK(ctx, cudaEventElapsedTime(&ms, ctx->prof_ev[2 * k], ctx->prof_ev[2 * k + 1]));
+            ctx->prof_ms += ms;
+            ctx->prof_count++;
+        }
+    }
     if (out.status == 0) out.status = 2;   // ran out of iterations without a flag (maxit reached)
     const int n = out.n;
-    std::vector<double> buf(3 * (size_t)maxit + 1);
-    // rho[0..n], alpha[0..n-1], beta[0..n-1]
-    if (n + 1 > kPinned - 64) return set_err(ctx, RMHMC_EINVAL, "Krylov run too long for the staging area");
-    RM_TRY(fetch(ctx, w.vals, buf.data(), n + 1, st));
+    // rho[0..n], alpha[0..n-1], beta[0..n-1] in one transfer of the scalar block
+    const int nvals = (maxit + 1) + 3 * maxit;
+    if (nvals > kPinned - 64) return set_err(ctx, RMHMC_EINVAL, "Krylov run too long for the staging area");
+    std::vector<double> buf(nvals);
+    RM_TRY(fetch(ctx, w.vals, buf.data(), nvals, st));
     out.rho.assign(buf.begin(), buf.begin() + n + 1);
-    out.alpha.resize(n);
-    out.beta.resize(n);
-    if (n > 0) {
-        RM_TRY(fetch(ctx, w.vals + (maxit + 1) + maxit, out.alpha.data(), n, st));
-        RM_TRY(fetch(ctx, w.vals + (maxit + 1) + 2 * maxit, out.beta.data(), n, st));
-    }
+    out.alpha.assign(buf.begin() + (maxit + 1) + maxit, buf.begin() + (maxit + 1) + maxit + n);
+    out.beta.assign(buf.begin() + (maxit + 1) + 2 * maxit, buf.begin() + (maxit + 1) + 2 * maxit + n);
     if (out.status == 3) return set_err(ctx, RMHMC_ENAN, "NaN/Inf in the Krylov recurrence");
     return RMHMC_OK;
 }
@@ -450,16 +482,15 @@ int krylov_combine(rmhmc_ctx* ctx, const CombineSpec& spec, TO* const* outs, cud
     int status = RMHMC_OK;
     const T* R = krylov_basis<T>(ctx);
     const size_t fs = field_elems(ctx);
-    const size_t npair = fs / 2;
     for (int m0 = 0; m0 < spec.M; m0 += kMaxCombine) {
         const int mc = std::min(kMaxCombine, spec.M - m0);
-        double* dcoef = (double*)workspace(ctx, "kr_coef", sizeof(double) * (size_t)kMaxCombine * spec.n, &status);
+        double* dcoef = (double*)workspace(ctx, "kr_coef", sizeof(double) * (size_t)kMaxCombine * kBasisCap, &status);
         if (!dcoef) return status;
         RM_TRY(upload(ctx, dcoef, spec.coef.data() + (size_t)m0 * spec.n, sizeof(double) * (size_t)mc * spec.n, st));
         OutPtrs<T, TO> op{};
         for (int m = 0; m < mc; m++) op.p[m] = outs[m0 + m];
-        const int grid = (int)((npair + kBlock - 1) / kBlock);
-        k_combine<T, TO><<<grid, kBlock, 0, st>>>(R, fs, spec.n, dcoef, mc, op, npair);
+        const int grid = (int)((fs + kBlock - 1) / kBlock);
+        k_combine<T, TO><<<grid, kBlock, 0, st>>>(R, fs, spec.n, dcoef, mc, op); ++ctx->launches;
         RM_LAUNCH_CHECK(ctx);
     }
     return RMHMC_OK;
@@ -472,10 +503,10 @@ int resid64(rmhmc_ctx* ctx, const double* b, const double* x, int nf, const doub
     double* dsig = (double*)workspace(ctx, "kr_sig", sizeof(double) * 64, &status);
     if (!dsig) return status;
     RM_TRY(upload(ctx, dsig, sigma, sizeof(double) * nf, st));
-    const dim3 grid(site_blocks(ctx), nf);
+    const dim3 grid(lane_blocks(ctx), nf);
     k_resid64<18><<<grid, kBlock, 0, st>>>(ctx->g, links64(ctx), b, x, dsig, r, field_elems(ctx),
                                            red_slot_partials(ctx, kSlotResid), red_slot_counter(ctx, kSlotResid),
-                                           red_slot_out(ctx, kSlotResid), (size_t)ctx->max_blocks * 8);
+                                           red_slot_out(ctx, kSlotResid), (size_t)ctx->max_blocks * 8); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     std::vector<double> tmp((size_t)nf * 8);
     RM_TRY(fetch(ctx, red_slot_out(ctx, kSlotResid), tmp.data(), nf * 8, st));
@@ -621,6 +652,36 @@ int solve_shifts(rmhmc_ctx* ctx, const MassTerm& m, const double* b, double tol,
     }
     if (iters) *iters = total;
     return RMHMC_OK;
+}
+
+int rational_apply(rmhmc_ctx* ctx, const MassTerm& m, const double* b, double tol, int maxiter, int prec, double* Y,
+                   int* iters, cudaStream_t st) {
+    const size_t fs = field_elems(ctx);
+    const int ns = m.npole();
+    int status = RMHMC_OK;
+    int it = 0;
+    double* xs = nullptr;
+    if (ns > 0) {
+        xs = (double*)workspace(ctx, "ra_xs", sizeof(double) * fs * ns, &status);
+        if (!xs) return status;
+        RM_TRY(solve_shifts(ctx, m, b, tol, maxiter, prec, xs, &it, nullptr, st));
+    }
+    RM_TRY(axpby64(ctx, m.c, b, 0.0, nullptr, Y, fs, st));
+    for (int j = 0; j < ns; j++) RM_TRY(axpby64(ctx, 1.0, Y, m.alpha[j], xs + (size_t)j * fs, Y, fs, st));
+    if (iters) *iters = it;
+    return RMHMC_OK;
+}
+
+int heatbath_apply(rmhmc_ctx* ctx, const MassTerm& m, const double* xi, double tol, int maxiter, int prec, double* P,
+                   cudaStream_t st) {
+    int status = RMHMC_OK;
+    const size_t fs = field_elems(ctx);
+    double* y = (double*)workspace(ctx, "hb_y", sizeof(double) * fs, &status);
+    if (!y) return status;
+    RM_TRY(rational_apply(ctx, m, xi, tol, maxiter, prec, y, nullptr, st));
+    // P = (1-kappa) y + kappa A y = ((1-kappa) + kappa/2) y - (kappa/16) H(y)
+    const double k = m.kappa;
+    return launch_lap(ctx, RMHMC_FP64, 18, y, P, 1, (1.0 - k) + 0.5 * k, -k / 16.0, nullptr, 0.0, -1, st);
 }
 
 }  // namespace rm

@@ -80,4 +80,11 @@ int solve_shifts(rmhmc_ctx* ctx, const MassTerm& m, const double* b, double tol,
 int kinetic_from_krylov(rmhmc_ctx* ctx, const MassTerm& m, const double* P, double tol, int maxiter, int prec,
                         double* F, double* Vel, double* T, int* iters, cudaStream_t st);
 
+// momentum heatbath P = m(A) R(A) xi, m(A) = (1-kappa) + kappa A (float64 in and out)
+int heatbath_apply(rmhmc_ctx* ctx, const MassTerm& m, const double* xi, double tol, int maxiter, int prec, double* P,
+                   cudaStream_t st);
+// Y = R(A) b (float64), every shift solved to relative true residual tol
+int rational_apply(rmhmc_ctx* ctx, const MassTerm& m, const double* b, double tol, int maxiter, int prec, double* Y,
+                   int* iters, cudaStream_t st);
+
 }  // namespace rm

@@ -1,7 +1,7 @@
 // Sec. 2, Eq. (3): the normalised adjoint covariant Laplacian A = -Delta_G/16 as a fused stencil
 //   Y = a X + b * H(X) + c W,   H(X)_mu(x) = sum_nu [U X(x+nu) U^dag + U^dag X(x-nu) U]
-// with optional per-field float64 sums <Y,Y> and <Y,X> (the Chebyshev moments).  One thread per
-// site computes all four components, so every link is loaded once per site.
+// with optional per-field float64 sums <Y,Y> and <Y,X> (the Chebyshev moments).  Four lanes per site,
+// one per field component (see stencil.cuh).
 #include "common.cuh"
 #include "ops.cuh"
 #include "stencil.cuh"
@@ -17,29 +17,27 @@ __global__ void __launch_bounds__(kBlock) k_lap(Geom g, typename LinksOf<T>::typ
     const int f = blockIdx.y;
     const T* Xf = X + f * fstride;
     T* Yf = Y + f * fstride;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = lane >> 2, mu = lane & 3;
     T dyy = T(0), dyx = T(0);
     if (s < g.V) {
-        herm<T> acc[4];
-        hop_sum4<T, LF>(g, U, s, SrcField<T>{Xf}, acc);
+        herm<T> acc;
+        hop_sum1<T, LF>(g, U, s, mu, SrcField<T>{Xf}, acc);
+        T h[8], x[8], y[8];
+        herm2_to_coef(acc, h);
+        load8(Xf + (size_t)s * 32 + mu * 8, x);
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            T h[8], x[8], y[8];
-            herm2_to_coef(acc[mu], h);
-            load8(Xf + (size_t)s * 32 + mu * 8, x);
+        for (int k = 0; k < 8; k++) y[k] = fma(b, h[k], a * x[k]);
+        if (HAS_W) {
+            T w[8];
+            load8(W + f * fstride + (size_t)s * 32 + mu * 8, w);
 #pragma unroll
-            for (int k = 0; k < 8; k++) y[k] = fma(b, h[k], a * x[k]);
-            if (HAS_W) {
-                T w[8];
-                load8(W + f * fstride + (size_t)s * 32 + mu * 8, w);
+            for (int k = 0; k < 8; k++) y[k] = fma(c, w[k], y[k]);
+        }
+        store8(Yf + (size_t)s * 32 + mu * 8, y);
+        if (DOTS) {
 #pragma unroll
-                for (int k = 0; k < 8; k++) y[k] = fma(c, w[k], y[k]);
-            }
-            store8(Yf + (size_t)s * 32 + mu * 8, y);
-            if (DOTS) {
-#pragma unroll
-                for (int k = 0; k < 8; k++) { dyy = fma(y[k], y[k], dyy); dyx = fma(y[k], x[k], dyx); }
-            }
+            for (int k = 0; k < 8; k++) { dyy = fma(y[k], y[k], dyy); dyx = fma(y[k], x[k], dyx); }
         }
     }
     if (DOTS) {
@@ -67,7 +65,7 @@ __global__ void __launch_bounds__(kBlock) k_lap(Geom g, typename LinksOf<T>::typ
 template <typename T, int LF>
 static int launch_lap_t(rmhmc_ctx* ctx, const T* X, T* Y, int nfield, double a, double b, const T* W, double c,
                         int slot, cudaStream_t st) {
-    const dim3 grid(site_blocks(ctx), nfield);
+    const dim3 grid(lane_blocks(ctx), nfield);
     const size_t fs = field_elems(ctx);
     const size_t ss = (size_t)ctx->max_blocks * 8;
     double* part = slot >= 0 ? red_slot_partials(ctx, slot) : nullptr;
@@ -82,6 +80,7 @@ static int launch_lap_t(rmhmc_ctx* ctx, const T* X, T* Y, int nfield, double a, 
         if (slot >= 0) k_lap<T, LF, false, true><<<grid, kBlock, 0, st>>>(ctx->g, U, X, Y, W, (T)a, (T)b, (T)c, fs, part, cnt, out, ss);
         else k_lap<T, LF, false, false><<<grid, kBlock, 0, st>>>(ctx->g, U, X, Y, W, (T)a, (T)b, (T)c, fs, part, cnt, out, ss);
     }
+    ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     return RMHMC_OK;
 }

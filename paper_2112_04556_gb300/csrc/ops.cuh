@@ -9,4 +9,12 @@ namespace rm {
 int launch_lap(rmhmc_ctx* ctx, int prec, int linkfmt, const void* X, void* Y, int nfield, double a, double b,
                const void* W, double c, int slot, cudaStream_t st);
 
+// gauge force F = -dS/dw (float64 output; arithmetic float64 or float32) from the context's links
+int gauge_force_launch(rmhmc_ctx* ctx, double beta, double c1, int prec, double* F, cudaStream_t st);
+// action S and average plaquette (float64, deterministic) from the context's float64 links
+int action_launch(rmhmc_ctx* ctx, double beta, double c1, double* S, double* plaq, cudaStream_t st);
+// G = sum_f w_f d<Z_f, A X_f>/dw (X, Z in the arithmetic precision, [nf][V][4][8]); G float64 [V][4][8]
+int link_grad_launch(rmhmc_ctx* ctx, int prec, const void* X, const void* Z, int nf, const double* w, double* G,
+                     cudaStream_t st);
+
 }  // namespace rm

@@ -1,8 +1,11 @@
-// The adjoint covariant hop sum of Sec. 2, Eq. (3) for one site and all four field components:
-//   acc_mu = 2 * sum_nu [ U_nu(x) X_mu(x+nu) U_nu(x)^dag + U_nu(x-nu)^dag X_mu(x-nu) U_nu(x-nu) ]
-// (the factor 2 comes from the doubled Hermitian expansion of the coefficients).  Every link of the
-// site is loaded once and applied to the four components; a field value is produced by the source
-// functor `src(site, mu, x[8])`, which lets callers fuse an axpy into the stencil's loads.
+// The adjoint covariant hop sum of Sec. 2, Eq. (3) for one site and one field component mu:
+//   acc = 2 * sum_nu [ U_nu(x) X_mu(x+nu) U_nu(x)^dag + U_nu(x-nu)^dag X_mu(x-nu) U_nu(x-nu) ]
+// (the factor 2 comes from the doubled Hermitian expansion of the coefficients).
+//
+// Thread layout of every stencil kernel: four consecutive lanes own one site, lane & 3 = mu.  A warp
+// therefore covers 8 consecutive sites; its loads of the 8 colour coefficients of X_mu at a neighbour
+// are one contiguous 1 KB segment of the [V][4][8] field, and its link loads hit 8 consecutive entries
+// of the structure-of-arrays link copy (the four lanes of a site read the same address).
 #pragma once
 #include "common.cuh"
 
@@ -13,32 +16,20 @@ template <> struct LinksOf<double> { using type = Links64; };
 template <> struct LinksOf<float> { using type = Links32; };
 
 template <typename T, int LF, class Src>
-__device__ __forceinline__ void hop_sum4(const Geom& g, const typename LinksOf<T>::type& U, int s,
-                                         const Src& src, herm<T> (&acc)[4]) {
+__device__ __forceinline__ void hop_sum1(const Geom& g, const typename LinksOf<T>::type& U, int s, int mu,
+                                         const Src& src, herm<T>& acc) {
     int fwd[4], bwd[4];
     neighbours(g, s, fwd, bwd);
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) acc[mu] = h_zero<T>();
+    acc = h_zero<T>();
 #pragma unroll
     for (int nu = 0; nu < 4; nu++) {
-        {
-            const mat3<T> u = LinkLoad<T, LF>::load(U, s, nu);
-#pragma unroll
-            for (int mu = 0; mu < 4; mu++) {
-                T x[8];
-                src(fwd[nu], mu, x);
-                acc_uxud(acc[mu], u, coef_to_herm2(x));
-            }
-        }
-        {
-            const mat3<T> u = LinkLoad<T, LF>::load(U, bwd[nu], nu);
-#pragma unroll
-            for (int mu = 0; mu < 4; mu++) {
-                T x[8];
-                src(bwd[nu], mu, x);
-                acc_udxu(acc[mu], u, coef_to_herm2(x));
-            }
-        }
+        T xf[8], xb[8];
+        src(fwd[nu], mu, xf);
+        src(bwd[nu], mu, xb);
+        const mat3<T> uf = LinkLoad<T, LF>::load(U, s, nu);
+        const mat3<T> ub = LinkLoad<T, LF>::load(U, bwd[nu], nu);
+        acc_uxud(acc, uf, coef_to_herm2(xf));
+        acc_udxu(acc, ub, coef_to_herm2(xb));
     }
 }
 

@@ -37,3 +37,21 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+_CONFIG2 = {}
+
+
+def config2_links():
+    """16^4 links from 20 plain-HMC trajectories of the oracle (beta = 6.0, tau = 1, 20 steps, Philox
+    momenta with seed 0, every trajectory accepted: thermalisation) started from the seed-0 random links
+    exp(i 0.3 sum r_a T_a)."""
+    if "U" not in _CONFIG2:
+        import oracle
+        from paper_2112_04556_gb300 import inputs
+        L = (16, 16, 16, 16)
+        U = inputs.random_links(L, eps=0.3, seed=0)
+        U, acc = oracle.plain_hmc(L, U, 20, 6.0, seed=0, tau=1.0, nsteps=20, metropolis=False)
+        _CONFIG2["U"] = U
+        _CONFIG2["acc"] = acc
+    return _CONFIG2["U"]

@@ -1,0 +1,153 @@
+"""GPU parity of the RMHMC trajectory pieces: Philox momenta, the exponential link update, the
+implicit leapfrog and the full trajectory; reversibility, dH ~ dtau^2, mixed vs float64 dH."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import dev, host, rel_l2, torch_cuda
+from oracle import fit
+from paper_2112_04556_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_gauss_field_matches_oracle():
+    import paper_2112_04556_gb300 as rm
+    L = (4, 4, 4, 6)
+    ref = oracle.gauss_field(L, 12345, 7, 0)
+    with rm.Context(L) as ctx:
+        g = host(rm.gauss_field(ctx, 12345, 7, 0))
+    assert np.abs(g - ref).max() <= 1e-13
+
+
+@pytest.mark.parametrize("eps", [1e-3, 0.05, 0.7, 3.0])
+def test_link_update_matches_oracle(eps):
+    import paper_2112_04556_gb300 as rm
+    L = (4, 4, 4, 4)
+    U = inputs.random_links(L, eps=0.5, seed=50)
+    V = inputs.gaussian_fields(L, 1, seed=51)[0]
+    ref = oracle.link_update(L, U, V, eps)
+    with rm.Context(L) as ctx:
+        out = host(rm.link_update(ctx, dev(U), dev(V), eps, reunit=False))
+        assert np.abs(out - ref).max() <= 1e-13
+        out2 = host(rm.link_update(ctx, dev(U), dev(V), eps, reunit=True))
+        assert np.abs(out2 - ref).max() <= 1e-13
+
+
+def _params(rm, mass, **kw):
+    d = dict(beta=6.0, c1=0.0, mass=mass, tau=0.2, nsteps=4, tol_md=1e-13, tol_h=1e-13, fp_tol=1e-13,
+             fp_maxit=100, maxiter=2000, prec=rm.FP64, seed=3, traj_index=0, metropolis=True)
+    d.update(kw)
+    return rm.make_params(**d)
+
+
+@pytest.mark.parametrize("L,npole,c1", [((2, 2, 2, 4), 12, 0.0), ((4, 4, 4, 4), 6, -0.331)])
+def test_md_parity(L, npole, c1):
+    import paper_2112_04556_gb300 as rm
+    U = inputs.random_links(L, eps=0.3, seed=52)
+    P = inputs.gaussian_fields(L, 1, seed=53)[0]
+    m = fit.mass_term(npole, 0.9)
+    U_ref, P_ref, its = oracle.md_trajectory(L, U, P, 0.2, 3, 6.0, c1, m, tol=1e-14, fp_tol=1e-13)
+    with rm.Context(L) as ctx:
+        Ud, Pd = dev(U), dev(P)
+        r = rm.md(ctx, Ud, Pd, _params(rm, m, c1=c1, nsteps=3))
+    assert np.abs(host(Ud) - U_ref).max() <= 1e-11
+    assert rel_l2(host(Pd), P_ref) <= 1e-10
+    assert r["fp_iters_p"] > 0 and r["fp_iters_u"] > 0
+
+
+def test_trajectory_parity():
+    import paper_2112_04556_gb300 as rm
+    L = (4, 4, 4, 4)
+    U = inputs.random_links(L, eps=0.3, seed=54)
+    xi = inputs.gaussian_fields(L, 1, seed=55)[0]
+    m = fit.mass_term(8, 0.9)
+    ref = oracle.trajectory(L, U, xi, 0.5, 0.2, 4, 6.0, 0.0, m, tol_md=1e-14, tol_h=1e-14, fp_tol=1e-13)
+    with rm.Context(L) as ctx:
+        Ud = dev(U)
+        r = rm.rmhmc_trajectory(ctx, Ud, _params(rm, m), xi=dev(xi))
+    assert abs(r["H0"] - ref["H0"]) <= 1e-12 * abs(ref["H0"])
+    assert abs(r["dH"] - ref["dH"]) <= 1e-8
+    assert abs(r["plaq"] - ref["plaq"]) <= 1e-12
+    if r["accepted"] == ref["accepted"]:
+        assert np.abs(host(Ud) - ref["U"]).max() <= 1e-11
+
+
+def test_identity_mass_trajectory_is_plain_hmc():
+    import paper_2112_04556_gb300 as rm
+    L = (4, 4, 4, 4)
+    U = inputs.random_links(L, eps=0.3, seed=56)
+    xi = oracle.gauss_field(L, 3, 0, 0)
+    ref = oracle.trajectory(L, U, xi, oracle.uniform(3, 0), 1.0, 10, 6.0, 0.0, oracle.identity_mass())
+    with rm.Context(L) as ctx:
+        Ud = dev(U)
+        r = rm.rmhmc_trajectory(ctx, Ud, _params(rm, {"c": 1.0, "alpha": [], "sigma": []}, tau=1.0, nsteps=10))
+    assert abs(r["u"] - oracle.uniform(3, 0)) == 0.0
+    assert abs(r["dH"] - ref["dH"]) <= 1e-9 and r["accepted"] == ref["accepted"]
+    assert np.abs(host(Ud) - ref["U"]).max() <= 1e-11
+
+
+def test_reversibility_gpu():
+    import paper_2112_04556_gb300 as rm
+    L = (6, 6, 6, 6)
+    U = inputs.random_links(L, eps=0.3, seed=57)
+    P = inputs.gaussian_fields(L, 1, seed=58)[0]
+    m = rm.mass_fit(12, 0.9)
+    with rm.Context(L) as ctx:
+        Ud, Pd = dev(U), dev(P)
+        p = _params(rm, m, tau=0.3, nsteps=3)
+        rm.md(ctx, Ud, Pd, p)
+        Pd.neg_()
+        rm.md(ctx, Ud, Pd, p)
+    assert np.abs(host(Ud) - U).max() <= 1e-10
+    assert np.abs(host(Pd) + P).max() <= 1e-9
+
+
+def test_dH_scales_with_step_squared():
+    import paper_2112_04556_gb300 as rm
+    L = (6, 6, 6, 6)
+    U = inputs.random_links(L, eps=0.3, seed=59)
+    xi = inputs.gaussian_fields(L, 1, seed=60)[0]
+    m = rm.mass_fit(12, 0.9)
+    dH = []
+    with rm.Context(L) as ctx:
+        for n in (4, 8):
+            r = rm.rmhmc_trajectory(ctx, dev(U), _params(rm, m, tau=0.4, nsteps=n, tol_md=1e-12, fp_tol=1e-12,
+                                                          metropolis=False), xi=dev(xi))
+            dH.append(r["dH"])
+    assert 3.0 < dH[0] / dH[1] < 5.0, dH
+
+
+def test_mixed_vs_fp64_dH_16_4():
+    """16^4 oracle-HMC links (beta = 6.0): the mixed-precision trajectory reproduces the float64 one,
+    |dH_mixed - dH_fp64| <= 1e-3, from the same links and momenta."""
+    import paper_2112_04556_gb300 as rm
+    from conftest import config2_links
+    L = (16, 16, 16, 16)
+    U = config2_links()
+    m = rm.mass_fit(12, 0.9)
+    out = {}
+    with rm.Context(L) as ctx:
+        for prec in (rm.FP64, rm.MIXED):
+            Ud = dev(U)
+            r = rm.rmhmc_trajectory(ctx, Ud, _params(rm, m, tau=0.5, nsteps=10, prec=prec, tol_md=1e-10 if prec == 0 else 1e-6,
+                                                     tol_h=1e-11, fp_tol=1e-10 if prec == 0 else 1e-6, metropolis=False))
+            out[prec] = (r, host(Ud))
+    assert abs(out[0][0]["dH"]) < 5.0, out[0][0]["dH"]
+    assert abs(out[1][0]["dH"] - out[0][0]["dH"]) <= 1e-3, (out[0][0]["dH"], out[1][0]["dH"])
+    assert abs(out[1][0]["plaq"] - out[0][0]["plaq"]) <= 1e-6
+    assert abs(out[1][0]["H0"] - out[0][0]["H0"]) <= 1e-9 * abs(out[0][0]["H0"])
+
+
+def test_trajectory_errors_leave_links_unchanged():
+    import paper_2112_04556_gb300 as rm
+    L = (4, 4, 4, 4)
+    U = inputs.random_links(L, eps=0.3, seed=61)
+    with rm.Context(L) as ctx:
+        Ud = dev(U)
+        with pytest.raises(rm.RmhmcError) as e:
+            rm.rmhmc_trajectory(ctx, Ud, _params(rm, rm.mass_fit(12, 0.9), fp_maxit=1, fp_tol=1e-15))
+        assert e.value.code == rm.ENOCONV
+        assert np.abs(host(Ud) - U).max() == 0.0
+        with pytest.raises(rm.RmhmcError):
+            rm.rmhmc_trajectory(ctx, Ud, _params(rm, rm.mass_fit(12, 0.9), nsteps=0))

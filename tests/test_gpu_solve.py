@@ -1,0 +1,107 @@
+"""GPU parity of the rational mass term (rat_mass_solve, heatbath) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import dev, host, rel_l2, torch_cuda
+from oracle import fit
+from paper_2112_04556_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (5, 3, 4, 7)])
+@pytest.mark.parametrize("prec,tol,bound", [(0, 1e-12, 1e-11), (1, 1e-10, 1e-9)])
+def test_rat_mass_solve_parity(L, prec, tol, bound):
+    import paper_2112_04556_gb300 as rm
+    U = inputs.random_links(L, eps=0.5, seed=21)
+    b = inputs.gaussian_fields(L, 1, seed=22)[0]
+    m = fit.mass_term(12, 0.9)
+    y_ref, xs_ref = oracle.rational_apply(L, U, b, m, tol=1e-14)
+    with rm.Context(L) as ctx:
+        y, xs, iters, resid = rm.rat_mass_solve(ctx, dev(U), dev(b), m, tol=tol, prec=prec, want_xs=True)
+        assert np.all(resid <= tol), resid
+        assert rel_l2(host(y), y_ref) <= bound
+        for j in range(12):
+            assert rel_l2(host(xs[j]), xs_ref[j]) <= 10 * bound
+        assert iters > 0
+
+
+def test_single_shift_is_plain_cg():
+    import paper_2112_04556_gb300 as rm
+    L = (4, 4, 4, 6)
+    U = inputs.random_links(L, eps=0.5, seed=23)
+    b = inputs.gaussian_fields(L, 1, seed=24)[0]
+    x_ref, _, _ = oracle.cg(lambda v: oracle.lap(L, U, v) + 0.3 * v, b, tol=1e-14)
+    with rm.Context(L) as ctx:
+        y, _, _, resid = rm.rat_mass_solve(ctx, dev(U), dev(b), {"c": 0.0, "alpha": [1.0], "sigma": [0.3]},
+                                          tol=1e-13, prec=rm.FP64)
+    assert rel_l2(host(y), x_ref) <= 1e-12 and resid[0] <= 1e-13
+
+
+def test_free_field_plane_wave():
+    """U = 1: R(A) T^a cos(k.x) = R(lambda_k) T^a cos(k.x) in both precisions."""
+    import paper_2112_04556_gb300 as rm
+    import helpers as H
+    L = (4, 4, 4, 8)
+    m = fit.mass_term(12, 0.9)
+    X = H.plane_wave(L, (1, 2, 0, 3), 1, 6, 0.2)
+    lam = H.free_eigenvalue(L, (1, 2, 0, 3))
+    with rm.Context(L) as ctx:
+        for prec, tol in ((0, 1e-13), (1, 1e-11)):
+            y, _, _, _ = rm.rat_mass_solve(ctx, dev(inputs.unit_links(L)), dev(X), m, tol=tol, prec=prec)
+            assert np.abs(host(y) - fit.evaluate(m, lam) * X).max() < 10 * tol
+
+
+def test_solve_config3_full_size():
+    """24^3 x 48, 12 poles (kappa = 0.9), float32 Krylov with float64 reliable updates to 1e-10:
+    reported residuals <= 1e-10, and the oracle recomputes b - (A + sigma_j) x_j at sampled sites."""
+    import paper_2112_04556_gb300 as rm
+    L = (24, 24, 24, 48)
+    V = int(np.prod(L))
+    U = inputs.random_links(L, eps=0.3, seed=0)
+    b = inputs.gaussian_fields(L, 1, seed=5)[0]
+    m = rm.mass_fit(12, 0.9)
+    rng = np.random.default_rng(6)
+    sites = np.unique(rng.integers(0, V, 3000))
+    with rm.Context(L) as ctx:
+        y, xs, iters, resid = rm.rat_mass_solve(ctx, dev(U), dev(b), m, tol=1e-10, prec=rm.MIXED, want_xs=True)
+        assert np.all(resid <= 1e-10), resid
+        for j in (0, 5, 11):
+            x = host(xs[j])
+            r = b[sites] - (oracle.lap_sites(L, U, x, sites) + m["sigma"][j] * x[sites])
+            assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(b[sites])
+        yy = host(y)
+        expect = m["c"] * b + sum(a * host(xs[j]) for j, a in enumerate(m["alpha"]))
+        assert rel_l2(yy, expect) <= 1e-14
+
+
+@pytest.mark.parametrize("prec,bound", [(0, 1e-11), (1, 1e-5)])
+def test_heatbath_parity(prec, bound):
+    import paper_2112_04556_gb300 as rm
+    L = (4, 4, 6, 4)
+    U = inputs.random_links(L, eps=0.5, seed=25)
+    xi = inputs.gaussian_fields(L, 1, seed=26)[0]
+    m = fit.mass_term(12, 0.9)
+    ref = oracle.heatbath(L, U, xi, m)
+    with rm.Context(L) as ctx:
+        P = rm.heatbath(ctx, dev(U), dev(xi), m, tol=1e-12 if prec == 0 else 1e-6, prec=prec)
+    assert rel_l2(host(P), ref) <= bound
+
+
+def test_solve_errors():
+    import paper_2112_04556_gb300 as rm
+    L = (4, 4, 4, 4)
+    b = dev(inputs.gaussian_fields(L, 1, seed=1)[0])
+    with rm.Context(L) as ctx:
+        Ud = dev(inputs.random_links(L, 0.5, 1))
+        with pytest.raises(rm.RmhmcError) as e:
+            rm.rat_mass_solve(ctx, Ud, b, {"c": 1.0, "alpha": [1.0], "sigma": [-0.1]})
+        assert e.value.code == rm.EINVAL
+        with pytest.raises(rm.RmhmcError) as e:
+            rm.rat_mass_solve(ctx, Ud, b, rm.mass_fit(12, 0.9), tol=1e-12, maxiter=2)
+        assert e.value.code == rm.ENOCONV
+        # zero right-hand side: zero solution, no iterations
+        z = b * 0
+        y, _, iters, resid = rm.rat_mass_solve(ctx, Ud, z, rm.mass_fit(12, 0.9))
+        assert iters == 0 and float(y.abs().max()) == 0.0
