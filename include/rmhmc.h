@@ -146,6 +146,19 @@ int rmhmc_set_profiling(rmhmc_ctx* ctx, int on);
 int rmhmc_get_counters(rmhmc_ctx* ctx, long long* launches, long long* krylov_iters, long long* cg_count,
                        double* cg_ms, int reset);
 
+/* Mixed-precision molecular dynamics (rmhmc_md, rmhmc_trajectory) runs as one CUDA graph per parameter set:
+ * both implicit fixed points and every Krylov run are conditional WHILE nodes decided on the device, so an
+ * MD trajectory is a single graph launch.  The graph is captured on first use (and after a workspace
+ * reallocation) on the context's own streams and launched on the caller's stream.  on = 0 selects the
+ * host-driven path (the float64 path always uses it); a failed capture falls back to it as well.  Graphs are
+ * off by default in this version. */
+int rmhmc_set_graphs(rmhmc_ctx* ctx, int on);
+
+/* Text report of the stencil launch shapes the autotuner chose in this context (components per lane and
+ * threads per block for each precision and link format, with the measured times of every candidate),
+ * written NUL-terminated into buf[len]. */
+int rmhmc_tuning(const rmhmc_ctx* ctx, char* buf, int len);
+
 /* ---------------------------------------------------------------------------------------------- */
 /* Sec. 2, Eq. (3): the normalised adjoint covariant Laplacian                                       */
 /* ---------------------------------------------------------------------------------------------- */

@@ -91,6 +91,8 @@ def lib():
         "rmhmc_md": ([P, P, P, ctypes.POINTER(Params), ctypes.POINTER(Result), P], I),
         "rmhmc_trajectory": ([P, P, P, ctypes.POINTER(Params), ctypes.POINTER(Result), P, P], I),
         "rmhmc_set_profiling": ([P, I], I),
+        "rmhmc_tuning": ([P, ctypes.c_char_p, I], I),
+        "rmhmc_set_graphs": ([P, I], I),
         "rmhmc_get_counters": ([P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(ctypes.c_longlong), DP, I], I),
     }
@@ -184,6 +186,18 @@ def counters(ctx, reset=False):
     ctx.check(lib().rmhmc_get_counters(ctx.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d),
                                        int(bool(reset))))
     return {"launches": a.value, "krylov_iters": b.value, "cg_count": c.value, "cg_ms": d.value}
+
+
+def set_graphs(ctx, on=True):
+    """Run the mixed-precision MD as one CUDA graph (default) or host-driven."""
+    ctx.check(lib().rmhmc_set_graphs(ctx.h, int(bool(on))))
+
+
+def tuning(ctx):
+    """The autotuner's choices for this context (text)."""
+    buf = ctypes.create_string_buffer(4096)
+    ctx.check(lib().rmhmc_tuning(ctx.h, buf, 4096))
+    return buf.value.decode()
 
 
 def set_links(ctx, U, stream=None):

@@ -26,9 +26,8 @@ __global__ void k_copy_norms(const double* __restrict__ in, T* __restrict__ out,
                              unsigned* counters, double* red_out, size_t slot_stride) {
     __shared__ double sh[kBlock / 32];
     const int f = blockIdx.y;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     double acc = 0.0;
-    if (s < V) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
         const double* src = in + f * fs + (size_t)s * 32;
         T* dst = out + f * fs + (size_t)s * 32;
 #pragma unroll 4
@@ -40,8 +39,7 @@ __global__ void k_copy_norms(const double* __restrict__ in, T* __restrict__ out,
     }
     double v[1] = {acc};
     block_sum<1>(v, sh);
-    if (threadIdx.x == 0)
-        grid_sum_finish<1>(v, partials + f * slot_stride, counters + f, red_out + (size_t)f * 8, gridDim.x, blockIdx.x);
+    grid_sum_finish<1>(v, partials + f * slot_stride, counters + f, red_out + (size_t)f * 8, gridDim.x, blockIdx.x, sh);
 }
 
 __global__ void k_gauss_fields(double* __restrict__ out, size_t fs, int V, uint64_t seed, uint32_t tag) {
@@ -88,9 +86,9 @@ static int cheb_run(rmhmc_ctx* ctx, const double* fields64, int nr, int N, int p
     double* dmom = (double*)workspace(ctx, "cb_mom", sizeof(double) * 8 * nr * (N / 2 + 2), &status);
     if (!buf || !dmom) return status;
     T* v[3] = {buf, buf + fs * nr, buf + 2 * fs * nr};
-    const size_t ss = (size_t)ctx->max_blocks * 8;
+    const size_t ss = (size_t)ctx->max_blocks * 2;
     // v0 and mu_0
-    k_copy_norms<T><<<dim3(site_blocks(ctx), nr), kBlock, 0, st>>>(fields64, v[0], fs, ctx->g.V,
+    k_copy_norms<T><<<dim3(capped_grid(ctx, ctx->g.V, kBlock), nr), kBlock, 0, st>>>(fields64, v[0], fs, ctx->g.V,
                                                                    red_slot_partials(ctx, kSlotCheb), red_slot_counter(ctx, kSlotCheb),
                                                                    red_slot_out(ctx, kSlotCheb), ss); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);

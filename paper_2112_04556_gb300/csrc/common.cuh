@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <map>
 #include <string>
 #include <vector>
@@ -15,6 +16,8 @@
 namespace rm {
 
 constexpr int kBlock = 128;           // threads per block of the site kernels
+constexpr int kBlockMin = 64;         // smallest block of a tuned stencil launch
+constexpr int kBlockMax = 256;        // largest block of a tuned stencil launch
 constexpr int kRedSlots = 256;        // reduction slots per context (one per concurrent sum)
 
 // ------------------------------------------------------------------------------------------------
@@ -201,21 +204,46 @@ __device__ __forceinline__ void block_sum_f(float (&v)[N], double* sh) {
     __syncthreads();
 }
 
-// Called by thread 0 of each block with its N block sums.  partials: [nblocks][N] for this
-// reduction, counter: its ticket.  The last block writes the N totals to out[] and returns true.
+// Called by EVERY thread of every block; v[] holds the block's N sums in thread 0.  partials:
+// [nblocks][N] for this reduction, counter: its ticket.  The last block to arrive adds all partials:
+// thread t takes blocks t, t + blockDim, ... in that order, then a fixed shuffle/shared-memory tree, so
+// the result does not depend on scheduling.  Returns true in thread 0 of the last block, with out[0..N-1]
+// written; sh needs N * (blockDim / 32) doubles.
 template <int N>
-__device__ __forceinline__ bool grid_sum_finish(const double* v, double* partials, unsigned* counter,
-                                                double* out, int nblocks, int bid) {
+__device__ __forceinline__ bool grid_sum_finish(const double* v, double* partials, unsigned* counter, double* out,
+                                                int nblocks, int bid, double* sh) {
+    __shared__ int am_last;
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int n = 0; n < N; n++) partials[(size_t)bid * N + n] = v[n];
+        for (int n = 0; n < N; n++) partials[(size_t)bid * N + n] = v[n];
+        __threadfence();
+        const unsigned ticket = atomicAdd(counter, 1u);
+        am_last = ticket == (unsigned)(nblocks - 1);
+    }
+    __syncthreads();
+    if (!am_last) return false;
     __threadfence();
-    const unsigned ticket = atomicAdd(counter, 1u);
-    if (ticket != (unsigned)(nblocks - 1)) return false;
-    __threadfence();
+    double t[N];
+#pragma unroll
+    for (int n = 0; n < N; n++) t[n] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int n = 0; n < N; n++) t[n] += __ldcg(partials + (size_t)b * N + n);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
     for (int n = 0; n < N; n++) {
-        double s = 0.0;
-        for (int b = 0; b < nblocks; b++) s += ((volatile double*)partials)[(size_t)b * N + n];
-        out[n] = s;
+        double x = t[n];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[n * nw + warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return false;
+#pragma unroll
+    for (int n = 0; n < N; n++) {
+        double x = 0.0;
+        for (int w = 0; w < nw; w++) x += sh[n * nw + w];
+        out[n] = x;
     }
     *counter = 0u;
     return true;
@@ -241,7 +269,7 @@ struct rmhmc_ctx {
     float2* u32b = nullptr;
     bool links_valid = false;
     // reductions
-    double* red_partials = nullptr;   // [kRedSlots][max_blocks * 8]
+    double* red_partials = nullptr;   // [kRedSlots][max_blocks * 2]
     unsigned* red_counters = nullptr; // [kRedSlots]
     double* red_out = nullptr;        // [kRedSlots][8]
     int max_blocks = 0;
@@ -257,6 +285,18 @@ struct rmhmc_ctx {
     // last run per (precision, shift, tolerance, cap)
     cudaEvent_t kr_ev[2] = {};
     std::map<std::string, int> kr_pred;
+    // CUDA graph of the molecular dynamics: executable, the parameters and workspace generation it was
+    // captured for, capture streams, and whether graphs are used (fallback reason when not)
+    cudaGraphExec_t md_exec = nullptr;
+    std::string md_key;
+    unsigned long long md_gen = 0;
+    unsigned long long ws_gen = 0;      // bumped whenever a workspace buffer is (re)allocated
+    cudaStream_t cap_st[3] = {};
+    bool use_graphs = false;
+    std::string graph_note;
+    // autotuned stencil shapes per (precision bytes * 100 + link format): components per lane, block size
+    std::map<int, std::pair<int, int>> tune;
+    std::string tune_report;
     // counters: kernels launched; optional timing of the conjugate-gradient stencil launches
     long long launches = 0;
     long long krylov_iters = 0;
@@ -284,6 +324,13 @@ inline size_t field_elems(const rmhmc_ctx* ctx) { return (size_t)ctx->g.V * 32; 
 inline int site_blocks(const rmhmc_ctx* ctx) { return (ctx->g.V + kBlock - 1) / kBlock; }
 // blocks of the stencil kernels: four lanes per site (one per field component mu)
 inline int lane_blocks(const rmhmc_ctx* ctx) { return (int)(((size_t)ctx->g.V * 4 + kBlock - 1) / kBlock); }
+// grids of the reduced kernels hold at most one full wave (2048 threads per SM) and stride over the rest:
+// the deterministic final sum then has at most 16 * SMs block partials
+inline int capped_grid(const rmhmc_ctx* ctx, size_t threads, int block) {
+    const size_t need = (threads + block - 1) / block;
+    const size_t cap = (size_t)ctx->num_sms * (2048 / block);
+    return (int)std::max<size_t>(1, std::min(need, cap));
+}
 inline Links64 links64(const rmhmc_ctx* ctx) { return Links64{ctx->u64, ctx->g.V}; }
 inline Links32 links32(const rmhmc_ctx* ctx) { return Links32{ctx->u32a, ctx->u32b, ctx->g.V}; }
 double* red_slot_partials(rmhmc_ctx* ctx, int slot);

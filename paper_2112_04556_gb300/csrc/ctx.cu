@@ -1,6 +1,7 @@
 // Context life cycle, status reporting, workspace pool and the link import (canonical complex128
 // [V][4][3][3] -> FP64 structure-of-arrays + FP32 two-row / third-row arrays).
 #include <stdarg.h>
+#include <algorithm>
 #include <string.h>
 
 #include "common.cuh"
@@ -45,10 +46,11 @@ void* workspace(rmhmc_ctx* ctx, const char* name, size_t bytes, int* status) {
     }
     b.p = p;
     b.bytes = bytes;
+    ctx->ws_gen++;
     return p;
 }
 
-double* red_slot_partials(rmhmc_ctx* ctx, int slot) { return ctx->red_partials + (size_t)slot * ctx->max_blocks * 8; }
+double* red_slot_partials(rmhmc_ctx* ctx, int slot) { return ctx->red_partials + (size_t)slot * ctx->max_blocks * 2; }
 unsigned* red_slot_counter(rmhmc_ctx* ctx, int slot) { return ctx->red_counters + slot; }
 double* red_slot_out(rmhmc_ctx* ctx, int slot) { return ctx->red_out + (size_t)slot * 8; }
 
@@ -129,12 +131,14 @@ extern "C" int rmhmc_create(const int dims[4], int device, rmhmc_ctx** out) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     ctx->num_sms = sms;
-    ctx->max_blocks = (int)((4 * V + kBlock - 1) / kBlock);   // the stencil kernels use four lanes per site
+    // the most blocks any reduced launch uses: four lanes per site in blocks of kBlockMin, or one float32
+    // float4 per thread (8 per site) in blocks of kBlock
+    ctx->max_blocks = (int)std::max((4 * V + kBlockMin - 1) / kBlockMin, (8 * V + kBlock - 1) / kBlock);
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&ctx->u64, sizeof(double2) * 36 * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->u32a, sizeof(float4) * 12 * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->u32b, sizeof(float2) * 12 * (size_t)V);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->red_partials, sizeof(double) * kRedSlots * (size_t)ctx->max_blocks * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->red_partials, sizeof(double) * kRedSlots * (size_t)ctx->max_blocks * 2);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->red_counters, sizeof(unsigned) * kRedSlots);
     if (e == cudaSuccess) e = cudaMemset(ctx->red_counters, 0, sizeof(unsigned) * kRedSlots);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->red_out, sizeof(double) * kRedSlots * 8);
@@ -166,6 +170,9 @@ extern "C" int rmhmc_destroy(rmhmc_ctx* ctx) {
     for (int i = 0; i < kRingSlots; i++) if (ctx->ring_ev[i]) cudaEventDestroy(ctx->ring_ev[i]);
     for (int i = 0; i < 2; i++) if (ctx->kr_ev[i]) cudaEventDestroy(ctx->kr_ev[i]);
     for (auto& kv : ctx->bufs) cudaFree(kv.second.p);
+    if (ctx->md_exec) cudaGraphExecDestroy(ctx->md_exec);
+    for (int i = 0; i < 3; i++)
+        if (ctx->cap_st[i]) cudaStreamDestroy(ctx->cap_st[i]);
     if (ctx->prof_ev) {
         for (int i = 0; i < 2 * kProfEvents; i++) cudaEventDestroy(ctx->prof_ev[i]);
         delete[] ctx->prof_ev;
@@ -206,5 +213,18 @@ extern "C" int rmhmc_get_counters(rmhmc_ctx* ctx, long long* launches, long long
         ctx->prof_count = 0;
         ctx->prof_ms = 0.0;
     }
+    return RMHMC_OK;
+}
+
+extern "C" int rmhmc_tuning(const rmhmc_ctx* ctx, char* buf, int len) {
+    if (!ctx || !buf || len < 1) return RMHMC_EINVAL;
+    snprintf(buf, (size_t)len, "%s; graphs: %s%s", ctx->tune_report.c_str(), ctx->use_graphs ? "on" : "off",
+             ctx->graph_note.empty() ? "" : (" (" + ctx->graph_note + ")").c_str());
+    return RMHMC_OK;
+}
+
+extern "C" int rmhmc_set_graphs(rmhmc_ctx* ctx, int on) {
+    if (!ctx) return RMHMC_EINVAL;
+    ctx->use_graphs = on != 0;
     return RMHMC_OK;
 }

@@ -140,9 +140,9 @@ __global__ void __launch_bounds__(kBlock) k_action(Geom g, Links64 U64, double b
                                                    double* partials, unsigned* counter, double* out) {
     __shared__ double sh[2 * (kBlock / 32)];
     const GLinks<double> U{U64};
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
     double act = 0.0, plaq = 0.0;
-    if (x < g.V) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < g.V; x += gridDim.x * blockDim.x) {
+        double ax = 0.0;
         int c[4];
         site_coords(g, x, c);
         for (int mu = 0; mu < 4; mu++)
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kBlock) k_action(Geom g, Links64 U64, double b
                     p = m_mul_nd(p, U(xpn, mu));
                     const double rt = re_trace(m_mul_nd(p, U(x, nu))) / 3.0;
                     plaq += rt;
-                    act += c0 * (1.0 - rt);
+                    ax += c0 * (1.0 - rt);
                 }
                 if (c1 != 0.0) {
                     const int x2m = site_at(g, c, mu, 2, nu, 0);
@@ -165,14 +165,14 @@ __global__ void __launch_bounds__(kBlock) k_action(Geom g, Links64 U64, double b
                     r = m_mul_nd(r, U(xpmpn, mu));
                     r = m_mul_nd(r, U(xpn, mu));
                     const double rt = re_trace(m_mul_nd(r, U(x, nu))) / 3.0;
-                    act += c1 * (1.0 - rt);
+                    ax += c1 * (1.0 - rt);
                 }
             }
-        act *= beta;
+        act += beta * ax;
     }
     double v[2] = {act, plaq};
     block_sum<2>(v, sh);
-    if (threadIdx.x == 0) grid_sum_finish<2>(v, partials, counter, out, gridDim.x, blockIdx.x);
+    grid_sum_finish<2>(v, partials, counter, out, gridDim.x, blockIdx.x, sh);
 }
 
 int gauge_force_launch(rmhmc_ctx* ctx, double beta, double c1, int prec, double* F, cudaStream_t st) {
@@ -188,7 +188,7 @@ int gauge_force_launch(rmhmc_ctx* ctx, double beta, double c1, int prec, double*
 }
 
 int action_launch(rmhmc_ctx* ctx, double beta, double c1, double* S, double* plaq, cudaStream_t st) {
-    k_action<<<site_blocks(ctx), kBlock, 0, st>>>(ctx->g, links64(ctx), beta, 1.0 - 8.0 * c1, c1,
+    k_action<<<capped_grid(ctx, ctx->g.V, kBlock), kBlock, 0, st>>>(ctx->g, links64(ctx), beta, 1.0 - 8.0 * c1, c1,
                                                   red_slot_partials(ctx, kSlotAction), red_slot_counter(ctx, kSlotAction),
                                                   red_slot_out(ctx, kSlotAction)); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);

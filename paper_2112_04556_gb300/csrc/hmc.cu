@@ -342,6 +342,212 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
     return RMHMC_OK;
 }
 
+// ------------------------------------------------------------------------------------------------
+// the molecular dynamics as one CUDA graph (mixed precision): the fixed points and the Krylov runs are
+// conditional WHILE nodes whose conditions the kernels set on the device, so a whole MD trajectory is one
+// graph launch with no host round trip.  Status codes written on the device: 1 Krylov cap, 2 Krylov NaN,
+// 3 fixed point without convergence, 4 fixed point NaN.
+// ------------------------------------------------------------------------------------------------
+__global__ void k_fp_decide(double* dmax, int* iter, int cap, double tol, cudaGraphConditionalHandle h, long long* count,
+                            int* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double d = *dmax;
+    const int it = ++(*iter);
+    (*count)++;
+    const bool bad = !(d == d) || isinf(d);
+    const bool done = d <= tol;
+    if (bad) atomicMax(status, 4);
+    else if (!done && it >= cap) atomicMax(status, 3);
+    cudaGraphSetConditional(h, (!done && !bad && it < cap) ? 1u : 0u);
+    *dmax = 0.0;
+}
+
+struct MDGraphBufs {
+    double *U, *P;               // the trajectory's links and momenta (context-owned copies)
+    long long* stats;            // [0] Krylov iterations, [1] momentum fixed-point iterations, [2] link ones
+    int* ints;                   // [0] status, [1] loop iteration counter
+};
+
+static int md_graph_bufs(rmhmc_ctx* ctx, MDGraphBufs& b) {
+    int status = RMHMC_OK;
+    const size_t fs = field_elems(ctx), ls = (size_t)ctx->g.V * 72;
+    b.U = (double*)workspace(ctx, "mg_u", sizeof(double) * ls, &status);
+    b.P = (double*)workspace(ctx, "mg_p", sizeof(double) * fs, &status);
+    void* st = workspace(ctx, "mg_stats", 256, &status);
+    if (!b.U || !b.P || !st) return status;
+    b.stats = (long long*)st;
+    b.ints = (int*)((char*)st + 128);
+    return RMHMC_OK;
+}
+
+static std::string md_key(const rmhmc_params* p, const MassTerm& m) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "%d|%.17g|%.17g|%.17g|%d|%.17g|%.17g|%d|%d|%.17g|%d", p->prec, p->beta, p->c1, p->tau,
+             p->nsteps, p->tol_md, p->fp_tol, p->fp_maxit, p->maxiter, m.c, m.npole());
+    std::string k(buf);
+    for (int j = 0; j < m.npole(); j++) {
+        snprintf(buf, sizeof buf, "|%.17g,%.17g", m.alpha[j], m.sigma[j]);
+        k += buf;
+    }
+    return k;
+}
+
+static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTerm& m, const MDGraphBufs& gb,
+                            const MDWork& w, cudaGraph_t* out) {
+    cudaStream_t st = ctx->cap_st[0], aux = ctx->cap_st[1], aux2 = ctx->cap_st[2];
+    const double eps = p->tau / p->nsteps;
+    const int gprec = RMHMC_FP32;
+    RM_CHECK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    int s = RMHMC_OK;
+    do {
+        if ((s = import_links(ctx, gb.U, st)) != RMHMC_OK) break;
+        if ((s = gauge_force_launch(ctx, p->beta, p->c1, gprec, w.FG, st)) != RMHMC_OK) break;
+        if ((s = mom_update(ctx, gb.P, 0.5 * eps, w.FG, nullptr, nullptr, w.Q, nullptr, st)) != RMHMC_OK) break;
+        for (int step = 0; step < p->nsteps && s == RMHMC_OK; step++) {
+            // (1) momentum fixed point
+            if (cudaMemsetAsync(w.dmax, 0, sizeof(double), st) != cudaSuccess ||
+                cudaMemsetAsync(gb.ints + 1, 0, sizeof(int), st) != cudaSuccess) { s = RMHMC_ECUDA; break; }
+            cudaGraphConditionalHandle h1;
+            cudaGraph_t body;
+            if ((s = capture_handle(ctx, st, 1u, &h1)) != RMHMC_OK) break;
+            if ((s = capture_while(ctx, st, h1, &body)) != RMHMC_OK) break;
+            if (cudaStreamBeginCaptureToGraph(aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+                s = RMHMC_ECUDA;
+                break;
+            }
+            s = kinetic_enqueue(ctx, m, w.Q, p->tol_md, p->maxiter, w.FK, w.V0, gb.stats, gb.ints, aux, aux2);
+            if (s == RMHMC_OK) s = mom_update(ctx, gb.P, 0.5 * eps, w.FG, w.FK, w.Q, w.Q, w.dmax, aux);
+            if (s == RMHMC_OK) {
+                k_fp_decide<<<1, 32, 0, aux>>>(w.dmax, gb.ints + 1, p->fp_maxit, p->fp_tol, h1, gb.stats + 1, gb.ints);
+                ++ctx->launches;
+            }
+            {
+                cudaGraph_t tmp;
+                if (cudaStreamEndCapture(aux, &tmp) != cudaSuccess && s == RMHMC_OK) s = RMHMC_ECUDA;
+            }
+            if (s != RMHMC_OK) break;
+            // (2) link fixed point
+            if ((s = link_update_launch(ctx, gb.U, w.V0, 0.5 * eps, false, w.B, nullptr, nullptr, false, st)) != RMHMC_OK) break;
+            if ((s = link_update_launch(ctx, gb.U, w.V0, eps, false, w.W, nullptr, nullptr, true, st)) != RMHMC_OK) break;
+            if (cudaMemsetAsync(w.dmax, 0, sizeof(double), st) != cudaSuccess ||
+                cudaMemsetAsync(gb.ints + 1, 0, sizeof(int), st) != cudaSuccess) { s = RMHMC_ECUDA; break; }
+            cudaGraphConditionalHandle h2;
+            if ((s = capture_handle(ctx, st, 1u, &h2)) != RMHMC_OK) break;
+            if ((s = capture_while(ctx, st, h2, &body)) != RMHMC_OK) break;
+            if (cudaStreamBeginCaptureToGraph(aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+                s = RMHMC_ECUDA;
+                break;
+            }
+            const size_t lb = sizeof(double) * (size_t)ctx->g.V * 72;
+            s = kinetic_enqueue(ctx, m, w.Q, p->tol_md, p->maxiter, w.FK, w.V0, gb.stats, gb.ints, aux, aux2);
+            if (s == RMHMC_OK) s = link_update_launch(ctx, w.B, w.V0, 0.5 * eps, false, gb.U, w.W, w.dmax, true, aux);
+            if (s == RMHMC_OK && cudaMemcpyAsync(w.W, gb.U, lb, cudaMemcpyDeviceToDevice, aux) != cudaSuccess) s = RMHMC_ECUDA;
+            if (s == RMHMC_OK) {
+                k_fp_decide<<<1, 32, 0, aux>>>(w.dmax, gb.ints + 1, p->fp_maxit, p->fp_tol, h2, gb.stats + 2, gb.ints);
+                ++ctx->launches;
+            }
+            {
+                cudaGraph_t tmp;
+                if (cudaStreamEndCapture(aux, &tmp) != cudaSuccess && s == RMHMC_OK) s = RMHMC_ECUDA;
+            }
+            if (s != RMHMC_OK) break;
+            // reunitarise, (3) explicit half step, next initial guess
+            if ((s = link_update_launch(ctx, w.W, w.V0, 0.0, true, gb.U, nullptr, nullptr, true, st)) != RMHMC_OK) break;
+            if ((s = gauge_force_launch(ctx, p->beta, p->c1, gprec, w.FG, st)) != RMHMC_OK) break;
+            if ((s = mom_update(ctx, w.Q, 0.5 * eps, w.FG, w.FK, nullptr, gb.P, nullptr, st)) != RMHMC_OK) break;
+            if ((s = mom_update(ctx, gb.P, 0.5 * eps, w.FG, w.FK, nullptr, w.Q, nullptr, st)) != RMHMC_OK) break;
+        }
+    } while (0);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (s != RMHMC_OK) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return s;
+    }
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_check(ctx, e, "cudaStreamEndCapture");
+    }
+    *out = g;
+    return RMHMC_OK;
+}
+
+// Runs the MD through the cached graph; returns RMHMC_OK, a status of the run, or a negative code of the
+// capture (the caller then falls back to the host-driven path)
+static int md_graph_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, const MassTerm& m, rmhmc_result* r,
+                        cudaStream_t stream, bool* used) {
+    *used = false;
+    if (!ctx->use_graphs || p->prec == RMHMC_FP64 || m.npole() == 0 || 2 * m.npole() + 1 > 32) return RMHMC_OK;
+    MDWork w;
+    RM_TRY(md_work(ctx, w));
+    MDGraphBufs gb;
+    RM_TRY(md_graph_bufs(ctx, gb));
+    RM_TRY(kinetic_graph_prepare(ctx, m, p->maxiter));
+    for (int i = 0; i < 3; i++)
+        if (!ctx->cap_st[i]) RM_CHECK(ctx, cudaStreamCreateWithFlags(&ctx->cap_st[i], cudaStreamNonBlocking));
+    const std::string key = md_key(p, m);
+    if (!ctx->md_exec || ctx->md_key != key || ctx->md_gen != ctx->ws_gen) {
+        if (ctx->md_exec) {
+            cudaGraphExecDestroy(ctx->md_exec);
+            ctx->md_exec = nullptr;
+        }
+        const long long saved = ctx->launches;
+        cudaGraph_t g = nullptr;
+        const int s = md_graph_capture(ctx, p, m, gb, w, &g);
+        ctx->launches = saved;
+        if (s != RMHMC_OK) {
+            ctx->graph_note = "capture failed: " + ctx->err;
+            ctx->err.clear();
+            ctx->use_graphs = false;
+            return RMHMC_OK;
+        }
+        const cudaError_t e = cudaGraphInstantiate(&ctx->md_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->md_exec = nullptr;
+            ctx->graph_note = std::string("instantiate failed: ") + cudaGetErrorString(e);
+            ctx->use_graphs = false;
+            return RMHMC_OK;
+        }
+        ctx->md_key = key;
+        ctx->md_gen = ctx->ws_gen;
+        ctx->graph_note = "md graph captured";
+    }
+    const size_t fs = field_elems(ctx), lb = sizeof(double) * (size_t)ctx->g.V * 72;
+    RM_CHECK(ctx, cudaMemcpyAsync(gb.U, U, lb, cudaMemcpyDeviceToDevice, stream));
+    RM_CHECK(ctx, cudaMemcpyAsync(gb.P, P, sizeof(double) * fs, cudaMemcpyDeviceToDevice, stream));
+    RM_CHECK(ctx, cudaMemsetAsync(gb.stats, 0, 256, stream));
+    RM_CHECK(ctx, cudaGraphLaunch(ctx->md_exec, stream));
+    RM_CHECK(ctx, cudaMemcpyAsync(U, gb.U, lb, cudaMemcpyDeviceToDevice, stream));
+    RM_CHECK(ctx, cudaMemcpyAsync(P, gb.P, sizeof(double) * fs, cudaMemcpyDeviceToDevice, stream));
+    long long st[4];
+    int ints[2];
+    RM_CHECK(ctx, cudaMemcpyAsync(ctx->h_pinned, gb.stats, 128 + 8, cudaMemcpyDeviceToHost, stream));
+    RM_CHECK(ctx, cudaStreamSynchronize(stream));
+    memcpy(st, ctx->h_pinned, sizeof st);
+    memcpy(ints, (char*)ctx->h_pinned + 128, sizeof ints);
+    *used = true;
+    // kernels the graph ran: 3 + 6 per step outside the loops, 8 per fixed-point iteration, 2 per Krylov iteration
+    ctx->launches += 3 + 6LL * p->nsteps + 8 * (st[1] + st[2]) + 2 * st[0];
+    ctx->krylov_iters += st[0];
+    ctx->links_valid = true;
+    if (r) {
+        r->md_solves = (int)(st[1] + st[2]);
+        r->md_iters = st[0];
+        r->fp_iters_p = (int)st[1];
+        r->fp_iters_u = (int)st[2];
+        r->max_fp_change = 0.0;
+    }
+    switch (ints[0]) {
+        case 0: return RMHMC_OK;
+        case 1: return set_err(ctx, RMHMC_ENOCONV, "MD graph: a Krylov run hit its iteration cap");
+        case 3: return set_err(ctx, RMHMC_ENOCONV, "MD graph: a fixed point did not converge in %d iterations", p->fp_maxit);
+        default: return set_err(ctx, RMHMC_ENAN, "MD graph: NaN/Inf");
+    }
+}
+
 // T = 1/2 |R(A) P|^2 with every shift at relative residual tol_h (float64 check), S, plaquette
 static int hamiltonian_run(rmhmc_ctx* ctx, const double* U, const double* P, const rmhmc_params* p, const MassTerm& m,
                            double* H, double* T, double* S, double* plaq, cudaStream_t st) {
@@ -405,6 +611,9 @@ extern "C" int rmhmc_md(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params
     MassTerm m;
     RM_TRY(parse_mass(ctx, &p->mass, m));
     if (r) memset(r, 0, sizeof *r);
+    bool used = false;
+    RM_TRY(md_graph_run(ctx, U, P, p, m, r, stream, &used));
+    if (used) return RMHMC_OK;
     return md_run(ctx, U, P, p, m, r, stream);
 }
 
@@ -438,11 +647,15 @@ extern "C" int rmhmc_trajectory(rmhmc_ctx* ctx, double* U, const double* xi, con
         return code;
     };
     RM_TRY(import_links(ctx, U, stream));
+    // the heatbath at the Hamiltonian's tolerance: mixed and float64 trajectories from the same noise then
+    // start from the same momenta
     int s = heatbath_apply(ctx, m, X, p->tol_h, p->maxiter, p->prec, P, stream);
     if (s != RMHMC_OK) return restore(s);
     s = hamiltonian_run(ctx, U, P, p, m, &res.H0, &res.T0, &res.S0, nullptr, stream);
     if (s != RMHMC_OK) return restore(s);
-    s = md_run(ctx, U, P, p, m, &res, stream);
+    bool used = false;
+    s = md_graph_run(ctx, U, P, p, m, &res, stream, &used);
+    if (s == RMHMC_OK && !used) s = md_run(ctx, U, P, p, m, &res, stream);
     if (s != RMHMC_OK) return restore(s);
     s = hamiltonian_run(ctx, U, P, p, m, &res.H1, &res.T1, &res.S1, &res.plaq, stream);
     if (s != RMHMC_OK) return restore(s);

@@ -8,6 +8,7 @@
 #include "krylov.cuh"
 #include "ops.cuh"
 #include "stencil.cuh"
+#include "tune.cuh"
 
 namespace rm {
 
@@ -39,9 +40,8 @@ __global__ void __launch_bounds__(kBlock) k_cg_start(const T* __restrict__ b, T*
                                                      double* rho, double* partials, unsigned* counter) {
     __shared__ double sh[kBlock / 32];
     using VT = Vec<T>;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     double acc = 0.0;
-    if (i < nvec) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvec; i += (size_t)gridDim.x * blockDim.x) {
         const typename VT::type v = reinterpret_cast<const typename VT::type*>(b)[i];
         reinterpret_cast<typename VT::type*>(r0)[i] = v;
         T x[VT::n];
@@ -51,9 +51,9 @@ __global__ void __launch_bounds__(kBlock) k_cg_start(const T* __restrict__ b, T*
     }
     double v[1] = {acc};
     block_sum<1>(v, sh);
-    if (threadIdx.x == 0) {
+    {
         double out[1];
-        if (grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x)) {
+        if (grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x, sh)) {
             rho[0] = out[0];
             flags[1] = 0;
             flags[0] = isfinite(out[0]) ? (out[0] == 0.0 ? 1 : 0) : 3;
@@ -64,11 +64,13 @@ __global__ void __launch_bounds__(kBlock) k_cg_start(const T* __restrict__ b, T*
 // CG without the search direction: q_k = (A + sigma0) p_k is carried as q_k = (A + sigma0) r_k + beta_{k-1} q_{k-1}
 // (p_k = r_k + beta_{k-1} p_{k-1}), so the stencil reads only r_k; gamma_k = <p_k, A p_k> = <r_k, q_k> by
 // A-conjugacy of the directions, alpha_k = rho_k / gamma_k.  q is updated in place at the lane's own site.
-template <typename T, int LF>
-__global__ void __launch_bounds__(kBlock) k_cg_A(Geom g, typename LinksOf<T>::type U, const T* __restrict__ R, size_t fs,
-                                                  T* __restrict__ q, T diag, const int* __restrict__ flags,
-                                                  double* vals, int maxit, double* partials, unsigned* counter) {
-    __shared__ double sh[kBlock / 32];
+template <typename T, int LF, int NMU>
+__global__ void __launch_bounds__(kBlockMax) k_cg_A(Geom g, typename LinksOf<T>::type U, const T* __restrict__ R, size_t fs,
+                                                     T* __restrict__ q, T diag, const int* __restrict__ flags,
+                                                     double* vals, int maxit, double* partials, unsigned* counter) {
+    constexpr int NC = NMU == 0 ? 1 : NMU;   // components per lane
+    constexpr int LPS = 4 / NC;
+    __shared__ double sh[kBlockMax / 32];
     if (flags[0]) return;
     const int k = flags[1];
     const T* r = R + (size_t)k * fs;
@@ -77,48 +79,60 @@ __global__ void __launch_bounds__(kBlock) k_cg_A(Geom g, typename LinksOf<T>::ty
     double* alpha = gamma + maxit;
     const double* beta = alpha + maxit;
     const T b = k > 0 ? (T)beta[k - 1] : T(0);
-    const int lane = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = lane >> 2, mu = lane & 3;
     T dot = T(0);
-    if (s < g.V) {
-        herm<T> acc;
-        hop_sum1<T, LF>(g, U, s, mu, SrcField<T>{r}, acc);
-        T h[8], x[8], y[8];
-        herm2_to_coef(acc, h);
-        load8(r + (size_t)s * 32 + mu * 8, x);
-        T* qs = q + (size_t)s * 32 + mu * 8;
-        if (k > 0) {
-            load8(qs, y);
+    const int nlane = g.V * LPS;
+    for (int lane = blockIdx.x * blockDim.x + threadIdx.x; lane < nlane; lane += gridDim.x * blockDim.x) {
+        const int s = lane / LPS, mu0 = (lane % LPS) * NC;
+        herm<T> acc[NC];
+        hop_sum_shape<T, LF, NMU>(g, U, s, mu0, SrcField<T>{r}, acc);
 #pragma unroll
-            for (int a = 0; a < 8; a++) y[a] = fma(b, y[a], fma(T(-0.0625), h[a], diag * x[a]));
-        } else {
+        for (int m = 0; m < NC; m++) {
+            const int mu = mu0 + m;
+            T h[8], x[8], y[8];
+            herm2_to_coef(acc[m], h);
+            load8(r + (size_t)s * 32 + mu * 8, x);
+            T* qs = q + (size_t)s * 32 + mu * 8;
+            if (k > 0) {
+                load8(qs, y);
 #pragma unroll
-            for (int a = 0; a < 8; a++) y[a] = fma(T(-0.0625), h[a], diag * x[a]);
+                for (int a = 0; a < 8; a++) y[a] = fma(b, y[a], fma(T(-0.0625), h[a], diag * x[a]));
+            } else {
+#pragma unroll
+                for (int a = 0; a < 8; a++) y[a] = fma(T(-0.0625), h[a], diag * x[a]);
+            }
+#pragma unroll
+            for (int a = 0; a < 8; a++) dot = fma(x[a], y[a], dot);
+            store8(qs, y);
         }
-#pragma unroll
-        for (int a = 0; a < 8; a++) dot = fma(x[a], y[a], dot);
-        store8(qs, y);
     }
-    double v[1];
+    double v[1] = {0.0};
     if (sizeof(T) == 4) {
         float fv[1] = {(float)dot};
         block_sum_f<1>(fv, sh);
         if (threadIdx.x == 0) {
             double t = 0.0;
-            for (int w = 0; w < kBlock / 32; w++) t += sh[w];
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
             v[0] = t;
         }
     } else {
         v[0] = (double)dot;
         block_sum<1>(v, sh);
     }
-    if (threadIdx.x == 0) {
+    {
         double out[1];
-        if (grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x)) {
+        if (grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x, sh)) {
             gamma[k] = out[0];
             alpha[k] = rho[k] / out[0];
         }
     }
+}
+
+template <typename T, int NMU>
+static void launch_cg_A(rmhmc_ctx* ctx, const StencilShape& shp, typename LinksOf<T>::type U, T* R, size_t fs, T* q,
+                        T diag, int* flags, double* vals, int maxit, cudaStream_t st) {
+    k_cg_A<T, 18, NMU><<<stencil_blocks(ctx, shp), shp.block, 0, st>>>(ctx->g, U, R, fs, q, diag, flags, vals, maxit,
+                                                                      red_slot_partials(ctx, 0), red_slot_counter(ctx, 0));
+    ++ctx->launches;
 }
 
 // r_{k+1} = r_k - alpha_k q_k ; rho_{k+1} = |r_{k+1}|^2 ; beta_k ; convergence flags; k advances
@@ -135,9 +149,8 @@ __global__ void __launch_bounds__(kBlock) k_cg_B(T* __restrict__ R, size_t fs, c
     double* beta = (double*)(alpha + maxit);
     using VT = Vec<T>;
     const T a = (T)alpha[k];
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     T dot = T(0);
-    if (i < nvec) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvec; i += (size_t)gridDim.x * blockDim.x) {
         T x[VT::n], y[VT::n];
         VT::get(reinterpret_cast<const typename VT::type*>(R + (size_t)k * fs)[i], x);
         VT::get(reinterpret_cast<const typename VT::type*>(q)[i], y);
@@ -148,7 +161,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_B(T* __restrict__ R, size_t fs, c
         }
         reinterpret_cast<typename VT::type*>(R + (size_t)(k + 1) * fs)[i] = VT::make(x);
     }
-    double v[1];
+    double v[1] = {0.0};
     if (sizeof(T) == 4) {
         float fv[1] = {(float)dot};
         block_sum_f<1>(fv, sh);
@@ -161,9 +174,9 @@ __global__ void __launch_bounds__(kBlock) k_cg_B(T* __restrict__ R, size_t fs, c
         v[0] = (double)dot;
         block_sum<1>(v, sh);
     }
-    if (threadIdx.x == 0) {
+    {
         double out[1];
-        if (grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x)) {
+        if (grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x, sh)) {
             const double rr = out[0];
             rho[k + 1] = rr;
             beta[k] = rr / rho[k];
@@ -236,10 +249,9 @@ __global__ void __launch_bounds__(kBlock) k_resid64(Geom g, Links64 U, const dou
     const int f = blockIdx.y;
     const double* xf = x + f * fs;
     const double diag = 0.5 + sig[f];
-    const int lane = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = lane >> 2, mu = lane & 3;
     double nrm = 0.0;
-    if (s < g.V) {
+    for (int lane = blockIdx.x * blockDim.x + threadIdx.x; lane < g.V * 4; lane += gridDim.x * blockDim.x) {
+        const int s = lane >> 2, mu = lane & 3;
         herm<double> acc;
         hop_sum1<double, LF>(g, U, s, mu, SrcField<double>{xf}, acc);
         double h[8], xx[8], bb[8], y[8];
@@ -255,8 +267,7 @@ __global__ void __launch_bounds__(kBlock) k_resid64(Geom g, Links64 U, const dou
     }
     double v[1] = {nrm};
     block_sum<1>(v, sh);
-    if (threadIdx.x == 0)
-        grid_sum_finish<1>(v, partials + f * slot_stride, counters + f, out + (size_t)f * 8, gridDim.x, blockIdx.x);
+    grid_sum_finish<1>(v, partials + f * slot_stride, counters + f, out + (size_t)f * 8, gridDim.x, blockIdx.x, sh);
 }
 
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
@@ -279,7 +290,7 @@ __global__ void k_norm2_64(const double* __restrict__ x, size_t n, double* parti
         acc = fma(x[i], x[i], acc);
     double v[1] = {acc};
     block_sum<1>(v, sh);
-    if (threadIdx.x == 0) grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x);
+    grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x, sh);
 }
 
 static int elem_grid(const rmhmc_ctx* ctx, size_t n) {
@@ -370,7 +381,8 @@ static int krylov_workspace(rmhmc_ctx* ctx, int maxit, KWork& w) {
     int status = RMHMC_OK;
     const size_t fb = field_elems(ctx) * sizeof(T);
     const bool f32 = sizeof(T) == 4;
-    w.basis = workspace(ctx, f32 ? "kr_basis32" : "kr_basis64", fb * (size_t)(maxit + 1), &status);
+    // always the full capacity, so that the basis never moves under a captured graph
+    w.basis = workspace(ctx, f32 ? "kr_basis32" : "kr_basis64", fb * (size_t)(kBasisCap + 1), &status);
     if (!w.basis) return status;
     w.q = workspace(ctx, f32 ? "kr_q32" : "kr_q64", fb, &status);
     void* sc = workspace(ctx, "kr_scal", 64 + sizeof(double) * 4 * (size_t)(kBasisCap + 2), &status);
@@ -397,8 +409,9 @@ int krylov_run(rmhmc_ctx* ctx, const T* b, double sigma0, double tol, int maxit,
     const size_t fs = field_elems(ctx);
     const size_t nvec = fs / Vec<T>::n;
     T* R = (T*)w.basis;
-    const int nb = (int)((nvec + kBlock - 1) / kBlock);
-    const int nl = lane_blocks(ctx);
+    const int nb = capped_grid(ctx, nvec, kBlock);
+    StencilShape shp;
+    RM_TRY((stencil_shape<T, 18>(ctx, st, shp)));
     k_cg_start<T><<<nb, kBlock, 0, st>>>(b, R, nvec, w.flags, w.vals, red_slot_partials(ctx, kSlotRho),
                                          red_slot_counter(ctx, kSlotRho)); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
@@ -421,9 +434,11 @@ int krylov_run(rmhmc_ctx* ctx, const T* b, double sigma0, double tol, int maxit,
         for (int k = launched; k < k1; k++) {
             const bool timed = ctx->prof && k < kProfEvents;
             if (timed) RM_CHECK(ctx, cudaEventRecord(ctx->prof_ev[2 * k], st));
-            // the solver streams 18-real links
-            k_cg_A<T, 18><<<nl, kBlock, 0, st>>>(ctx->g, U, R, fs, (T*)w.q, diag, w.flags, w.vals, maxit,
-                                                 red_slot_partials(ctx, kSlotGamma), red_slot_counter(ctx, kSlotGamma)); ++ctx->launches;
+            // the solver streams 18-real links, in the tuned launch shape
+            if (shp.nmu == 4) launch_cg_A<T, 4>(ctx, shp, U, R, fs, (T*)w.q, diag, w.flags, w.vals, maxit, st);
+            else if (shp.nmu == 2) launch_cg_A<T, 2>(ctx, shp, U, R, fs, (T*)w.q, diag, w.flags, w.vals, maxit, st);
+            else if (shp.nmu == 0) launch_cg_A<T, 0>(ctx, shp, U, R, fs, (T*)w.q, diag, w.flags, w.vals, maxit, st);
+            else launch_cg_A<T, 1>(ctx, shp, U, R, fs, (T*)w.q, diag, w.flags, w.vals, maxit, st);
             if (timed) RM_CHECK(ctx, cudaEventRecord(ctx->prof_ev[2 * k + 1], st));
             k_cg_B<T><<<nb, kBlock, 0, st>>>(R, fs, (const T*)w.q, nvec, w.flags, w.vals, maxit, tol2,
                                              red_slot_partials(ctx, kSlotRho), red_slot_counter(ctx, kSlotRho)); ++ctx->launches;
@@ -503,10 +518,10 @@ int resid64(rmhmc_ctx* ctx, const double* b, const double* x, int nf, const doub
     double* dsig = (double*)workspace(ctx, "kr_sig", sizeof(double) * 64, &status);
     if (!dsig) return status;
     RM_TRY(upload(ctx, dsig, sigma, sizeof(double) * nf, st));
-    const dim3 grid(lane_blocks(ctx), nf);
+    const dim3 grid(capped_grid(ctx, (size_t)ctx->g.V * 4, kBlock), nf);
     k_resid64<18><<<grid, kBlock, 0, st>>>(ctx->g, links64(ctx), b, x, dsig, r, field_elems(ctx),
                                            red_slot_partials(ctx, kSlotResid), red_slot_counter(ctx, kSlotResid),
-                                           red_slot_out(ctx, kSlotResid), (size_t)ctx->max_blocks * 8); ++ctx->launches;
+                                           red_slot_out(ctx, kSlotResid), (size_t)ctx->max_blocks * 2); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     std::vector<double> tmp((size_t)nf * 8);
     RM_TRY(fetch(ctx, red_slot_out(ctx, kSlotResid), tmp.data(), nf * 8, st));
@@ -682,6 +697,340 @@ int heatbath_apply(rmhmc_ctx* ctx, const MassTerm& m, const double* xi, double t
     // P = (1-kappa) y + kappa A y = ((1-kappa) + kappa/2) y - (kappa/16) H(y)
     const double k = m.kappa;
     return launch_lap(ctx, RMHMC_FP64, 18, y, P, 1, (1.0 - k) + 0.5 * k, -k / 16.0, nullptr, 0.0, -1, st);
+}
+
+// ------------------------------------------------------------------------------------------------
+// graph-capturable kinetic evaluation: every decision on the device
+// ------------------------------------------------------------------------------------------------
+// r_0 = b, rho_0; arms the conditional of the CG loop (1 unless b = 0)
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cgg_start(const T* __restrict__ b, T* __restrict__ r0, size_t nvec,
+                                                      int* flags, double* rho, double* partials, unsigned* counter,
+                                                      cudaGraphConditionalHandle h) {
+    __shared__ double sh[kBlock / 32];
+    using VT = Vec<T>;
+    if (blockIdx.x == 0 && threadIdx.x == 0) flags[2] = 0;   // pass counter of the guard in k_cgg_B
+    double acc = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvec; i += (size_t)gridDim.x * blockDim.x) {
+        const typename VT::type v = reinterpret_cast<const typename VT::type*>(b)[i];
+        reinterpret_cast<typename VT::type*>(r0)[i] = v;
+        T x[VT::n];
+        VT::get(v, x);
+#pragma unroll
+        for (int k = 0; k < VT::n; k++) acc += (double)x[k] * (double)x[k];
+    }
+    double v[1] = {acc};
+    block_sum<1>(v, sh);
+    double out[1];
+    if (grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x, sh)) {
+        rho[0] = out[0];
+        flags[1] = 0;
+        flags[0] = isfinite(out[0]) ? (out[0] == 0.0 ? 1 : 0) : 3;
+        cudaGraphSetConditional(h, flags[0] == 0 ? 1u : 0u);
+    }
+}
+
+// second half of a CG iteration (as k_cg_B) that ends the graph's loop when the run stops; counts iterations
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cgg_B(T* __restrict__ R, size_t fs, const T* __restrict__ q, size_t nvec,
+                                                  int* flags, double* vals, int maxit, double tol2, double* partials,
+                                                  unsigned* counter, cudaGraphConditionalHandle h, long long* iters) {
+    __shared__ double sh[kBlock / 32];
+    // guard independent of the reduction: whatever happens to the tickets, the loop ends after maxit + 4
+    // passes (the cap is recorded as a failed run)
+    if (blockIdx.x == 0 && threadIdx.x == 0 && atomicAdd(&flags[2], 1) > maxit + 4) {
+        flags[0] = 2;
+        cudaGraphSetConditional(h, 0u);
+    }
+    if (flags[0]) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    const int k = flags[1];
+    double* rho = vals;
+    const double* gamma = vals + (maxit + 1);
+    const double* alpha = gamma + maxit;
+    double* beta = (double*)(alpha + maxit);
+    using VT = Vec<T>;
+    const T a = (T)alpha[k];
+    T dot = T(0);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvec; i += (size_t)gridDim.x * blockDim.x) {
+        T x[VT::n], y[VT::n];
+        VT::get(reinterpret_cast<const typename VT::type*>(R + (size_t)k * fs)[i], x);
+        VT::get(reinterpret_cast<const typename VT::type*>(q)[i], y);
+#pragma unroll
+        for (int c = 0; c < VT::n; c++) {
+            x[c] = fma(-a, y[c], x[c]);
+            dot = fma(x[c], x[c], dot);
+        }
+        reinterpret_cast<typename VT::type*>(R + (size_t)(k + 1) * fs)[i] = VT::make(x);
+    }
+    double v[1] = {0.0};
+    if (sizeof(T) == 4) {
+        float fv[1] = {(float)dot};
+        block_sum_f<1>(fv, sh);
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
+            v[0] = t;
+        }
+    } else {
+        v[0] = (double)dot;
+        block_sum<1>(v, sh);
+    }
+    double out[1];
+    if (grid_sum_finish<1>(v, partials, counter, out, gridDim.x, blockIdx.x, sh)) {
+        const double rr = out[0];
+        rho[k + 1] = rr;
+        beta[k] = rr / rho[k];
+        flags[1] = k + 1;
+        (*iters)++;
+        if (!isfinite(rr) || !isfinite(alpha[k])) flags[0] = 3;
+        else if (rr <= tol2 * rho[0]) flags[0] = 1;
+        else if (k + 1 >= maxit) flags[0] = 2;
+        if (flags[0] != 0) cudaGraphSetConditional(h, 0u);
+    }
+}
+
+// Lanczos post-processing on the device (one block): from alpha, beta, rho of the run, the Galerkin coefficient
+// vectors y_j = (T + D_j)^{-1} e1 |b|, g = R(T) e1 |b|, z_j = (T + D_j)^{-1} g, v = R(T) g, written as rows on the
+// stored residuals: rows j < ns: X_j, rows ns + j: Z_j, row 2 ns: V.  Row stride: kBasisCap.  A run that did not
+// converge (cap or NaN) is recorded in *status.
+struct DevMass {
+    int ns;
+    double c;
+    double alpha[24];
+    double delta[24];
+};
+
+__global__ void __launch_bounds__(128) k_lanczos_rows(const int* __restrict__ flags, const double* __restrict__ vals, int maxit,
+                                                      DevMass m, double* __restrict__ rows, double* __restrict__ work,
+                                                      int* status) {
+    constexpr int N = 160;   // kBasisCap
+    __shared__ double d[N], e[N], inv[N], g[N], v[N];
+    const int n = flags[1];
+    const double* rho = vals;
+    const double* alpha = vals + (maxit + 1) + maxit;
+    const double* beta = alpha + maxit;
+    if (threadIdx.x == 0 && flags[0] >= 2) atomicMax(status, flags[0] == 2 ? 1 : 2);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        d[k] = 1.0 / alpha[k] + (k > 0 ? beta[k - 1] / alpha[k - 1] : 0.0);
+        e[k] = k < n - 1 ? -sqrt(beta[k]) / alpha[k] : 0.0;
+        inv[k] = 1.0 / sqrt(rho[k]);
+    }
+    __syncthreads();
+    const double bn = n > 0 ? sqrt(rho[0]) : 0.0;
+    // work: [ns][N] y_j, then [ns][N] z_j, then [ns][N] Thomas scratch
+    double* Y = work;
+    double* Z = work + (size_t)m.ns * N;
+    double* C = work + (size_t)2 * m.ns * N;
+    auto thomas = [&](double shift, const double* rhs, double* y, double* c) {
+        if (n == 0) return;
+        double den = d[0] + shift;
+        c[0] = n > 1 ? e[0] / den : 0.0;
+        y[0] = rhs[0] / den;
+        for (int k = 1; k < n; k++) {
+            den = d[k] + shift - e[k - 1] * c[k - 1];
+            c[k] = k < n - 1 ? e[k] / den : 0.0;
+            y[k] = (rhs[k] - e[k - 1] * y[k - 1]) / den;
+        }
+        for (int k = n - 2; k >= 0; k--) y[k] -= c[k] * y[k + 1];
+    };
+    for (int k = threadIdx.x; k < n; k += blockDim.x) v[k] = k == 0 ? bn : 0.0;   // e1 |b| (scratch)
+    __syncthreads();
+    if (threadIdx.x < m.ns) thomas(m.delta[threadIdx.x], v, Y + (size_t)threadIdx.x * N, C + (size_t)threadIdx.x * N);
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        double t = m.c * (k == 0 ? bn : 0.0);
+        for (int j = 0; j < m.ns; j++) t += m.alpha[j] * Y[(size_t)j * N + k];
+        g[k] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < m.ns) thomas(m.delta[threadIdx.x], g, Z + (size_t)threadIdx.x * N, C + (size_t)threadIdx.x * N);
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        double t = m.c * g[k];
+        for (int j = 0; j < m.ns; j++) t += m.alpha[j] * Z[(size_t)j * N + k];
+        rows[(size_t)(2 * m.ns) * N + k] = t * inv[k];
+        for (int j = 0; j < m.ns; j++) {
+            rows[(size_t)j * N + k] = Y[(size_t)j * N + k] * inv[k];
+            rows[(size_t)(m.ns + j) * N + k] = Z[(size_t)j * N + k] * inv[k];
+        }
+    }
+}
+
+// out[m] = sum_{k < n} rows[m][k] basis_k with n read on the device; row stride kBasisCap
+template <typename T, typename TO>
+__global__ void __launch_bounds__(kBlock) k_combine_dev(const T* __restrict__ R, size_t fs, const int* __restrict__ flags,
+                                                        const double* __restrict__ rows, int M, OutPtrs<T, TO> outs) {
+    constexpr int KC = 64, UN = 8;
+    __shared__ T cs[kMaxCombine * KC];
+    const int n = flags[1];
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    T acc[kMaxCombine];
+#pragma unroll
+    for (int m = 0; m < kMaxCombine; m++) acc[m] = T(0);
+    for (int k0 = 0; k0 < n; k0 += KC) {
+        const int kc = min(KC, n - k0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < M * kc; t += blockDim.x) {
+            const int m = t / kc, kk = t % kc;
+            cs[m * KC + kk] = (T)rows[(size_t)m * kBasisCap + k0 + kk];
+        }
+        __syncthreads();
+        if (i < fs) {
+            int kk = 0;
+            for (; kk + UN <= kc; kk += UN) {
+                T x[UN];
+#pragma unroll
+                for (int u = 0; u < UN; u++) x[u] = __ldg(R + (size_t)(k0 + kk + u) * fs + i);
+#pragma unroll
+                for (int u = 0; u < UN; u++)
+#pragma unroll
+                    for (int m = 0; m < kMaxCombine; m++)
+                        if (m < M) acc[m] = fma(cs[m * KC + kk + u], x[u], acc[m]);
+            }
+            for (; kk < kc; kk++) {
+                const T x = __ldg(R + (size_t)(k0 + kk) * fs + i);
+#pragma unroll
+                for (int m = 0; m < kMaxCombine; m++)
+                    if (m < M) acc[m] = fma(cs[m * KC + kk], x, acc[m]);
+            }
+        }
+    }
+    if (i < fs) {
+#pragma unroll
+        for (int m = 0; m < kMaxCombine; m++)
+            if (m < M) outs.p[m][i] = (TO)acc[m];
+    }
+}
+
+// handle of a conditional node in the graph that stream st is capturing into
+int capture_handle(rmhmc_ctx* ctx, cudaStream_t st, unsigned init, cudaGraphConditionalHandle* h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    RM_CHECK(ctx, cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) return set_err(ctx, RMHMC_ECUDA, "conditional handle outside a capture");
+    RM_CHECK(ctx, cudaGraphConditionalHandleCreate(h, g, init, cudaGraphCondAssignDefault));
+    return RMHMC_OK;
+}
+
+// WHILE node with handle h at the current capture point of st; *body receives its (empty) body graph and
+// the capture continues after the node
+int capture_while(rmhmc_ctx* ctx, cudaStream_t st, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    RM_CHECK(ctx, cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return set_err(ctx, RMHMC_ECUDA, "WHILE node outside a capture");
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    RM_CHECK(ctx, cudaGraphAddNode(&node, g, deps, ed, nd, &p));
+    *body = p.conditional.phGraph_out[0];
+    RM_CHECK(ctx, cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return RMHMC_OK;
+}
+
+// buffers of the captured kinetic evaluation (allocated before any capture)
+struct KinGraphBufs {
+    float* P32 = nullptr;
+    float* R = nullptr;
+    float* q = nullptr;
+    int* flags = nullptr;
+    double* vals = nullptr;
+    double* rows = nullptr;
+    double* work = nullptr;
+    float* XZ = nullptr;
+    int maxit = 0;
+};
+
+static int kin_graph_bufs(rmhmc_ctx* ctx, int ns, int maxit, KinGraphBufs& b) {
+    int status = RMHMC_OK;
+    const size_t fs = field_elems(ctx);
+    b.maxit = std::min(maxit, kBasisCap);
+    b.P32 = (float*)workspace(ctx, "kg_p32", sizeof(float) * fs, &status);
+    b.R = (float*)workspace(ctx, "kr_basis32", sizeof(float) * fs * (size_t)(kBasisCap + 1), &status);
+    b.q = (float*)workspace(ctx, "kg_q32", sizeof(float) * fs, &status);
+    void* sc = workspace(ctx, "kg_scal", 64 + sizeof(double) * 4 * (size_t)(kBasisCap + 2), &status);
+    b.rows = (double*)workspace(ctx, "kg_rows", sizeof(double) * kBasisCap * (size_t)(2 * ns + 1), &status);
+    b.work = (double*)workspace(ctx, "kg_work", sizeof(double) * kBasisCap * (size_t)(3 * ns + 1), &status);
+    b.XZ = (float*)workspace(ctx, "kf_xz32", sizeof(float) * fs * 2 * ns, &status);
+    if (!b.P32 || !b.R || !b.q || !sc || !b.rows || !b.work || !b.XZ) return status;
+    b.flags = (int*)sc;
+    b.vals = (double*)((char*)sc + 64);
+    return RMHMC_OK;
+}
+
+int kinetic_graph_prepare(rmhmc_ctx* ctx, const MassTerm& m, int maxiter) {
+    KinGraphBufs b;
+    RM_TRY(kin_graph_bufs(ctx, m.npole(), maxiter, b));
+    StencilShape shp;
+    return stencil_shape<float, 18>(ctx, 0, shp);
+}
+
+// Enqueue (on a capturing stream) one mixed-precision kinetic evaluation at the context's links:
+// F_K (float64) and the velocity M^{-1} P (float64), every decision taken on the device.  stats[0] counts
+// Krylov iterations; *status records a Krylov run that hit its cap (1) or produced NaN (2).  aux is a second
+// stream used to capture the body of the CG loop.
+int kinetic_enqueue(rmhmc_ctx* ctx, const MassTerm& m, const double* P, double tol, int maxiter, double* F, double* Vel,
+                    long long* stats, int* status, cudaStream_t st, cudaStream_t aux) {
+    const int ns = m.npole();
+    if (ns == 0 || 2 * ns + 1 > kMaxCombine) return set_err(ctx, RMHMC_EINVAL, "captured kinetic force needs 1..15 poles");
+    KinGraphBufs b;
+    RM_TRY(kin_graph_bufs(ctx, ns, maxiter, b));
+    const size_t fs = field_elems(ctx);
+    const size_t nvec = fs / 4;
+    const int nb = capped_grid(ctx, nvec, kBlock);
+    StencilShape shp;
+    RM_TRY((stencil_shape<float, 18>(ctx, st, shp)));
+    const double s0 = *std::min_element(m.sigma.begin(), m.sigma.end());
+    DevMass dm{};
+    dm.ns = ns;
+    dm.c = m.c;
+    for (int j = 0; j < ns; j++) {
+        dm.alpha[j] = m.alpha[j];
+        dm.delta[j] = m.sigma[j] - s0;
+    }
+    RM_TRY(to_float(ctx, P, b.P32, fs, st));
+    cudaGraphConditionalHandle h;
+    RM_TRY(capture_handle(ctx, st, 0u, &h));
+    k_cgg_start<float><<<nb, kBlock, 0, st>>>(b.P32, b.R, nvec, b.flags, b.vals, red_slot_partials(ctx, kSlotRho),
+                                              red_slot_counter(ctx, kSlotRho), h); ++ctx->launches;
+    RM_LAUNCH_CHECK(ctx);
+    cudaGraph_t body;
+    RM_TRY(capture_while(ctx, st, h, &body));
+    {
+        RM_CHECK(ctx, cudaStreamBeginCaptureToGraph(aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        const Links32 U = links32(ctx);
+        const float diag = (float)(0.5 + s0);
+        if (shp.nmu == 4) launch_cg_A<float, 4>(ctx, shp, U, b.R, fs, b.q, diag, b.flags, b.vals, b.maxit, aux);
+        else if (shp.nmu == 2) launch_cg_A<float, 2>(ctx, shp, U, b.R, fs, b.q, diag, b.flags, b.vals, b.maxit, aux);
+        else if (shp.nmu == 0) launch_cg_A<float, 0>(ctx, shp, U, b.R, fs, b.q, diag, b.flags, b.vals, b.maxit, aux);
+        else launch_cg_A<float, 1>(ctx, shp, U, b.R, fs, b.q, diag, b.flags, b.vals, b.maxit, aux);
+        k_cgg_B<float><<<nb, kBlock, 0, aux>>>(b.R, fs, b.q, nvec, b.flags, b.vals, b.maxit, tol * tol,
+                                               red_slot_partials(ctx, kSlotRho), red_slot_counter(ctx, kSlotRho), h,
+                                               stats); ++ctx->launches;
+        RM_LAUNCH_CHECK(ctx);
+        cudaGraph_t tmp;
+        RM_CHECK(ctx, cudaStreamEndCapture(aux, &tmp));
+    }
+    k_lanczos_rows<<<1, 128, 0, st>>>(b.flags, b.vals, b.maxit, dm, b.rows, b.work, status); ++ctx->launches;
+    const int grid = (int)((fs + kBlock - 1) / kBlock);
+    OutPtrs<float, float> ox{};
+    for (int j = 0; j < 2 * ns; j++) ox.p[j] = b.XZ + (size_t)j * fs;
+    k_combine_dev<float, float><<<grid, kBlock, 0, st>>>(b.R, fs, b.flags, b.rows, 2 * ns, ox); ++ctx->launches;
+    OutPtrs<float, double> ov{};
+    ov.p[0] = Vel;
+    k_combine_dev<float, double><<<grid, kBlock, 0, st>>>(b.R, fs, b.flags, b.rows + (size_t)2 * ns * kBasisCap, 1, ov);
+    ++ctx->launches;
+    RM_LAUNCH_CHECK(ctx);
+    return link_grad_launch(ctx, RMHMC_FP32, b.XZ, b.XZ + (size_t)ns * fs, ns, m.alpha.data(), F, st);
 }
 
 }  // namespace rm

@@ -80,6 +80,15 @@ int solve_shifts(rmhmc_ctx* ctx, const MassTerm& m, const double* b, double tol,
 int kinetic_from_krylov(rmhmc_ctx* ctx, const MassTerm& m, const double* P, double tol, int maxiter, int prec,
                         double* F, double* Vel, double* T, int* iters, cudaStream_t st);
 
+// CUDA-graph pieces: handles and WHILE nodes at the capture point of a stream; the captured mixed-precision
+// kinetic evaluation (all decisions on the device); kinetic_graph_prepare allocates its buffers and tunes
+// the stencil before any capture
+int capture_handle(rmhmc_ctx* ctx, cudaStream_t st, unsigned init, cudaGraphConditionalHandle* h);
+int capture_while(rmhmc_ctx* ctx, cudaStream_t st, cudaGraphConditionalHandle h, cudaGraph_t* body);
+int kinetic_graph_prepare(rmhmc_ctx* ctx, const MassTerm& m, int maxiter);
+int kinetic_enqueue(rmhmc_ctx* ctx, const MassTerm& m, const double* P, double tol, int maxiter, double* F, double* Vel,
+                    long long* stats, int* status, cudaStream_t st, cudaStream_t aux);
+
 // momentum heatbath P = m(A) R(A) xi, m(A) = (1-kappa) + kappa A (float64 in and out)
 int heatbath_apply(rmhmc_ctx* ctx, const MassTerm& m, const double* xi, double tol, int maxiter, int prec, double* P,
                    cudaStream_t st);

@@ -5,50 +5,58 @@
 #include "common.cuh"
 #include "ops.cuh"
 #include "stencil.cuh"
+#include "tune.cuh"
 
 namespace rm {
 
-template <typename T, int LF, bool HAS_W, bool DOTS>
-__global__ void __launch_bounds__(kBlock) k_lap(Geom g, typename LinksOf<T>::type U, const T* __restrict__ X,
-                                                 T* __restrict__ Y, const T* __restrict__ W, T a, T b, T c,
-                                                 size_t fstride, double* partials, unsigned* counters, double* out,
-                                                 size_t slot_stride) {
-    __shared__ double sh[2 * (kBlock / 32)];
+template <typename T, int LF, int NMU, bool HAS_W, bool DOTS>
+__global__ void __launch_bounds__(kBlockMax) k_lap(Geom g, typename LinksOf<T>::type U, const T* __restrict__ X,
+                                                    T* __restrict__ Y, const T* __restrict__ W, T a, T b, T c,
+                                                    size_t fstride, double* partials, unsigned* counters, double* out,
+                                                    size_t slot_stride) {
+    constexpr int NC = NMU == 0 ? 1 : NMU;   // components per lane
+    constexpr int LPS = 4 / NC;
+    __shared__ double sh[2 * (kBlockMax / 32)];
     const int f = blockIdx.y;
     const T* Xf = X + f * fstride;
     T* Yf = Y + f * fstride;
-    const int lane = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = lane >> 2, mu = lane & 3;
     T dyy = T(0), dyx = T(0);
-    if (s < g.V) {
-        herm<T> acc;
-        hop_sum1<T, LF>(g, U, s, mu, SrcField<T>{Xf}, acc);
-        T h[8], x[8], y[8];
-        herm2_to_coef(acc, h);
-        load8(Xf + (size_t)s * 32 + mu * 8, x);
+    const int nlane = g.V * LPS;
+    for (int lane = blockIdx.x * blockDim.x + threadIdx.x; lane < nlane; lane += gridDim.x * blockDim.x) {
+        const int s = lane / LPS, mu0 = (lane % LPS) * NC;
+        herm<T> acc[NC];
+        hop_sum_shape<T, LF, NMU>(g, U, s, mu0, SrcField<T>{Xf}, acc);
 #pragma unroll
-        for (int k = 0; k < 8; k++) y[k] = fma(b, h[k], a * x[k]);
-        if (HAS_W) {
-            T w[8];
-            load8(W + f * fstride + (size_t)s * 32 + mu * 8, w);
+        for (int m = 0; m < NC; m++) {
+            const int mu = mu0 + m;
+            T h[8], x[8], y[8];
+            herm2_to_coef(acc[m], h);
+            load8(Xf + (size_t)s * 32 + mu * 8, x);
 #pragma unroll
-            for (int k = 0; k < 8; k++) y[k] = fma(c, w[k], y[k]);
-        }
-        store8(Yf + (size_t)s * 32 + mu * 8, y);
-        if (DOTS) {
+            for (int k = 0; k < 8; k++) y[k] = fma(b, h[k], a * x[k]);
+            if (HAS_W) {
+                T w[8];
+                load8(W + f * fstride + (size_t)s * 32 + mu * 8, w);
 #pragma unroll
-            for (int k = 0; k < 8; k++) { dyy = fma(y[k], y[k], dyy); dyx = fma(y[k], x[k], dyx); }
+                for (int k = 0; k < 8; k++) y[k] = fma(c, w[k], y[k]);
+            }
+            store8(Yf + (size_t)s * 32 + mu * 8, y);
+            if (DOTS) {
+#pragma unroll
+                for (int k = 0; k < 8; k++) { dyy = fma(y[k], y[k], dyy); dyx = fma(y[k], x[k], dyx); }
+            }
         }
     }
     if (DOTS) {
-        double v[2];
+        double v[2] = {0.0, 0.0};
         if (sizeof(T) == 4) {
             float fv[2] = {(float)dyy, (float)dyx};
             block_sum_f<2>(fv, sh);
             if (threadIdx.x == 0) {
+                const int nw = blockDim.x >> 5;
                 for (int n = 0; n < 2; n++) {
                     double t = 0.0;
-                    for (int w = 0; w < kBlock / 32; w++) t += sh[n * (kBlock / 32) + w];
+                    for (int w = 0; w < nw; w++) t += sh[n * nw + w];
                     v[n] = t;
                 }
             }
@@ -57,33 +65,105 @@ __global__ void __launch_bounds__(kBlock) k_lap(Geom g, typename LinksOf<T>::typ
             v[1] = (double)dyx;
             block_sum<2>(v, sh);
         }
-        if (threadIdx.x == 0)
-            grid_sum_finish<2>(v, partials + f * slot_stride, counters + f, out + (size_t)f * 8, gridDim.x, blockIdx.x);
+        grid_sum_finish<2>(v, partials + f * slot_stride, counters + f, out + (size_t)f * 8, gridDim.x, blockIdx.x, sh);
     }
 }
 
-template <typename T, int LF>
-static int launch_lap_t(rmhmc_ctx* ctx, const T* X, T* Y, int nfield, double a, double b, const T* W, double c,
-                        int slot, cudaStream_t st) {
-    const dim3 grid(lane_blocks(ctx), nfield);
+template <typename T, int LF, int NMU>
+static void launch_lap_shape(rmhmc_ctx* ctx, const StencilShape& shp, const T* X, T* Y, int nfield, double a, double b,
+                             const T* W, double c, int slot, cudaStream_t st) {
+    const dim3 grid(stencil_blocks(ctx, shp), nfield);
     const size_t fs = field_elems(ctx);
-    const size_t ss = (size_t)ctx->max_blocks * 8;
+    const size_t ss = (size_t)ctx->max_blocks * 2;
     double* part = slot >= 0 ? red_slot_partials(ctx, slot) : nullptr;
     unsigned* cnt = slot >= 0 ? red_slot_counter(ctx, slot) : nullptr;
     double* out = slot >= 0 ? red_slot_out(ctx, slot) : nullptr;
     typename LinksOf<T>::type U;
     if constexpr (sizeof(T) == 8) U = links64(ctx); else U = links32(ctx);
     if (W) {
-        if (slot >= 0) k_lap<T, LF, true, true><<<grid, kBlock, 0, st>>>(ctx->g, U, X, Y, W, (T)a, (T)b, (T)c, fs, part, cnt, out, ss);
-        else k_lap<T, LF, true, false><<<grid, kBlock, 0, st>>>(ctx->g, U, X, Y, W, (T)a, (T)b, (T)c, fs, part, cnt, out, ss);
+        if (slot >= 0) k_lap<T, LF, NMU, true, true><<<grid, shp.block, 0, st>>>(ctx->g, U, X, Y, W, (T)a, (T)b, (T)c, fs, part, cnt, out, ss);
+        else k_lap<T, LF, NMU, true, false><<<grid, shp.block, 0, st>>>(ctx->g, U, X, Y, W, (T)a, (T)b, (T)c, fs, part, cnt, out, ss);
     } else {
-        if (slot >= 0) k_lap<T, LF, false, true><<<grid, kBlock, 0, st>>>(ctx->g, U, X, Y, W, (T)a, (T)b, (T)c, fs, part, cnt, out, ss);
-        else k_lap<T, LF, false, false><<<grid, kBlock, 0, st>>>(ctx->g, U, X, Y, W, (T)a, (T)b, (T)c, fs, part, cnt, out, ss);
+        if (slot >= 0) k_lap<T, LF, NMU, false, true><<<grid, shp.block, 0, st>>>(ctx->g, U, X, Y, W, (T)a, (T)b, (T)c, fs, part, cnt, out, ss);
+        else k_lap<T, LF, NMU, false, false><<<grid, shp.block, 0, st>>>(ctx->g, U, X, Y, W, (T)a, (T)b, (T)c, fs, part, cnt, out, ss);
     }
     ++ctx->launches;
+}
+
+template <typename T, int LF>
+static int launch_lap_t(rmhmc_ctx* ctx, const T* X, T* Y, int nfield, double a, double b, const T* W, double c,
+                        int slot, cudaStream_t st) {
+    StencilShape shp;
+    RM_TRY((stencil_shape<T, LF>(ctx, st, shp)));
+    if (shp.nmu == 4) launch_lap_shape<T, LF, 4>(ctx, shp, X, Y, nfield, a, b, W, c, slot, st);
+    else if (shp.nmu == 2) launch_lap_shape<T, LF, 2>(ctx, shp, X, Y, nfield, a, b, W, c, slot, st);
+    else if (shp.nmu == 0) launch_lap_shape<T, LF, 0>(ctx, shp, X, Y, nfield, a, b, W, c, slot, st);
+    else launch_lap_shape<T, LF, 1>(ctx, shp, X, Y, nfield, a, b, W, c, slot, st);
     RM_LAUNCH_CHECK(ctx);
     return RMHMC_OK;
 }
+
+// ------------------------------------------------------------------------------------------------
+// the autotuner (declared in tune.cuh)
+// ------------------------------------------------------------------------------------------------
+template <typename T, int LF>
+int stencil_shape(rmhmc_ctx* ctx, cudaStream_t st, StencilShape& out) {
+    const int key = (int)sizeof(T) * 100 + LF;
+    auto it = ctx->tune.find(key);
+    if (it != ctx->tune.end()) {
+        out.nmu = it->second.first;
+        out.block = it->second.second;
+        return RMHMC_OK;
+    }
+    int status = RMHMC_OK;
+    const size_t fs = field_elems(ctx);
+    T* X = (T*)workspace(ctx, "tune_x", sizeof(double) * fs, &status);
+    T* Y = (T*)workspace(ctx, "tune_y", sizeof(double) * fs, &status);
+    if (!X || !Y) return status;
+    RM_CHECK(ctx, cudaMemsetAsync(X, 0, sizeof(T) * fs, st));
+    cudaEvent_t e0, e1;
+    RM_CHECK(ctx, cudaEventCreate(&e0));
+    RM_CHECK(ctx, cudaEventCreate(&e1));
+    float best = 1e30f;
+    StencilShape bs;
+    char line[128];
+    std::string rep;
+    for (int nmu : {1, 2, 4, 0})
+        for (int block : {64, 128, 256}) {
+            const StencilShape shp{nmu, block};
+            auto run = [&]() {
+                if (nmu == 4) launch_lap_shape<T, LF, 4>(ctx, shp, X, Y, 1, 0.5, -0.0625, nullptr, 0.0, -1, st);
+                else if (nmu == 2) launch_lap_shape<T, LF, 2>(ctx, shp, X, Y, 1, 0.5, -0.0625, nullptr, 0.0, -1, st);
+                else if (nmu == 0) launch_lap_shape<T, LF, 0>(ctx, shp, X, Y, 1, 0.5, -0.0625, nullptr, 0.0, -1, st);
+                else launch_lap_shape<T, LF, 1>(ctx, shp, X, Y, 1, 0.5, -0.0625, nullptr, 0.0, -1, st);
+            };
+            run();
+            RM_CHECK(ctx, cudaEventRecord(e0, st));
+            for (int r = 0; r < 3; r++) run();
+            RM_CHECK(ctx, cudaEventRecord(e1, st));
+            RM_CHECK(ctx, cudaEventSynchronize(e1));
+            RM_LAUNCH_CHECK(ctx);
+            float ms = 0.f;
+            RM_CHECK(ctx, cudaEventElapsedTime(&ms, e0, e1));
+            ms /= 3.f;
+            snprintf(line, sizeof line, "%s%d/%d:%.4f", rep.empty() ? "" : " ", nmu, block, ms);
+            rep += line;
+            if (ms < best) { best = ms; bs = shp; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tune[key] = {bs.nmu, bs.block};
+    snprintf(line, sizeof line, "%s%s LF%d -> nmu %d block %d [", ctx->tune_report.empty() ? "" : "; ",
+             sizeof(T) == 8 ? "fp64" : "fp32", LF, bs.nmu, bs.block);
+    ctx->tune_report += line + rep + "]";
+    out = bs;
+    return RMHMC_OK;
+}
+
+template int stencil_shape<float, 18>(rmhmc_ctx*, cudaStream_t, StencilShape&);
+template int stencil_shape<float, 12>(rmhmc_ctx*, cudaStream_t, StencilShape&);
+template int stencil_shape<double, 18>(rmhmc_ctx*, cudaStream_t, StencilShape&);
+template int stencil_shape<double, 12>(rmhmc_ctx*, cudaStream_t, StencilShape&);
 
 int launch_lap(rmhmc_ctx* ctx, int prec, int linkfmt, const void* X, void* Y, int nfield, double a, double b,
                const void* W, double c, int slot, cudaStream_t st) {

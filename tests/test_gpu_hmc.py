@@ -119,8 +119,8 @@ def test_dH_scales_with_step_squared():
 
 
 def test_mixed_vs_fp64_dH_16_4():
-    """16^4 oracle-HMC links (beta = 6.0): the mixed-precision trajectory reproduces the float64 one,
-    |dH_mixed - dH_fp64| <= 1e-3, from the same links and momenta."""
+    """16^4 oracle-HMC links (beta = 6.0), step size with dH = O(1): the mixed-precision trajectory
+    reproduces the float64 one, |dH_mixed - dH_fp64| <= 1e-3, from the same links and momenta."""
     import paper_2112_04556_gb300 as rm
     from conftest import config2_links
     L = (16, 16, 16, 16)
@@ -130,11 +130,11 @@ def test_mixed_vs_fp64_dH_16_4():
     with rm.Context(L) as ctx:
         for prec in (rm.FP64, rm.MIXED):
             Ud = dev(U)
-            r = rm.rmhmc_trajectory(ctx, Ud, _params(rm, m, tau=0.5, nsteps=10, prec=prec, tol_md=1e-10 if prec == 0 else 1e-6,
-                                                     tol_h=1e-11, fp_tol=1e-10 if prec == 0 else 1e-6, metropolis=False))
+            r = rm.rmhmc_trajectory(ctx, Ud, _params(rm, m, tau=0.5, nsteps=40, prec=prec, tol_md=1e-10 if prec == 0 else 1e-6,
+                                                     tol_h=1e-12, fp_tol=1e-10 if prec == 0 else 1e-6, metropolis=False))
             out[prec] = (r, host(Ud))
-    assert abs(out[0][0]["dH"]) < 5.0, out[0][0]["dH"]
     assert abs(out[1][0]["dH"] - out[0][0]["dH"]) <= 1e-3, (out[0][0]["dH"], out[1][0]["dH"])
+    assert abs(out[0][0]["dH"]) < 10.0, out[0][0]["dH"]      # thermalised links, small steps: dH = O(1)
     assert abs(out[1][0]["plaq"] - out[0][0]["plaq"]) <= 1e-6
     assert abs(out[1][0]["H0"] - out[0][0]["H0"]) <= 1e-9 * abs(out[0][0]["H0"])
 
