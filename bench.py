@@ -228,6 +228,8 @@ def main():
     ap.add_argument("--dims", default="32,32,32,32")
     ap.add_argument("--nsteps", type=int, default=NSTEPS)
     ap.add_argument("--therm", type=int, default=20, help="plain-HMC thermalisation trajectories")
+    ap.add_argument("--graphs", choices=["on", "off"], default="on",
+                    help="run the mixed-precision MD as one CUDA graph per trajectory")
     args = ap.parse_args()
     global DIMS
     DIMS = tuple(int(v) for v in args.dims.split(","))
@@ -258,6 +260,7 @@ def main():
     stream = torch.cuda.current_stream()
     V = int(np.prod(DIMS))
     lat = rm.Context(DIMS, device=local)
+    rm.set_graphs(lat, args.graphs == "on")
     mass = rm.mass_fit(NPOLE, KAPPA)
     seeds = replica_seeds(rank)
     U = torch.from_numpy(inputs.random_links(DIMS, eps=0.3, seed=seeds["links"])).cuda()

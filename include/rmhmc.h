@@ -151,7 +151,7 @@ int rmhmc_get_counters(rmhmc_ctx* ctx, long long* launches, long long* krylov_it
  * MD trajectory is a single graph launch.  The graph is captured on first use (and after a workspace
  * reallocation) on the context's own streams and launched on the caller's stream.  on = 0 selects the
  * host-driven path (the float64 path always uses it); a failed capture falls back to it as well.  Graphs are
- * off by default in this version. */
+ * on by default. */
 int rmhmc_set_graphs(rmhmc_ctx* ctx, int on);
 
 /* Text report of the stencil launch shapes the autotuner chose in this context (components per lane and

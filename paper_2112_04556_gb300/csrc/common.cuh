@@ -292,7 +292,7 @@ struct rmhmc_ctx {
     unsigned long long md_gen = 0;
     unsigned long long ws_gen = 0;      // bumped whenever a workspace buffer is (re)allocated
     cudaStream_t cap_st[3] = {};
-    bool use_graphs = false;
+    bool use_graphs = true;
     std::string graph_note;
     // autotuned stencil shapes per (precision bytes * 100 + link format): components per lane, block size
     std::map<int, std::pair<int, int>> tune;

@@ -30,18 +30,27 @@ constexpr int kSlotMax = 60;
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ void expi_coeffs(double c0, double c1, cplx<double> f[3]) {
     if (c1 < 0.25) {
-        double a = 1.0, b = 0.0, c = 0.0;   // Q^n = a I + b Q + c Q^2
-        cplx<double> t = cmk(1.0, 0.0);     // i^n / n!
-        f[0] = cmk(0.0, 0.0); f[1] = cmk(0.0, 0.0); f[2] = cmk(0.0, 0.0);
-        for (int n = 0; n < 40; n++) {
-            f[0] = cadd(f[0], cscale(t, a));
-            f[1] = cadd(f[1], cscale(t, b));
-            f[2] = cadd(f[2], cscale(t, c));
-            const double an = c0 * c, bn = a + c1 * c, cn = b;
+        // f_k = sum_n (i^n / n!) {a_n, b_n, c_n}_k with Q^n = a_n I + b_n Q + c_n Q^2.  The eigenvalues of
+        // Q are below sqrt(4 c1 / 3) < 1 in modulus, so |a_n| + |b_n| + |c_n| bounds the size of Q^n and the
+        // sum stops once a term falls below 1e-18; 1/n! are compile-time constants (no division)
+        double fr0 = 0.0, fr1 = 0.0, fr2 = 0.0, fi0 = 0.0, fi1 = 0.0, fi2 = 0.0;
+        double a = 1.0, b = 0.0, c = 0.0;
+        double inv = 1.0;   // 1/n!
+#pragma unroll
+        for (int n = 0; n < 26; n++) {
+            const double sa = inv * a, sb = inv * b, sc = inv * c;
+            switch (n & 3) {   // i^n = 1, i, -1, -i
+                case 0: fr0 += sa; fr1 += sb; fr2 += sc; break;
+                case 1: fi0 += sa; fi1 += sb; fi2 += sc; break;
+                case 2: fr0 -= sa; fr1 -= sb; fr2 -= sc; break;
+                default: fi0 -= sa; fi1 -= sb; fi2 -= sc; break;
+            }
+            if (n >= 3 && (fabs(sa) + fabs(sb) + fabs(sc)) < 1e-18) break;
+            const double an = c0 * c, bn = fma(c1, c, a), cn = b;
             a = an; b = bn; c = cn;
-            t = cscale(cmk(-t.im, t.re), 1.0 / (n + 1));   // t * i / (n+1)
-            if (fabs(t.re) + fabs(t.im) < 1e-18 && n > 2) break;
+            inv *= 1.0 / (double)(n + 1);
         }
+        f[0] = cmk(fr0, fi0); f[1] = cmk(fr1, fi1); f[2] = cmk(fr2, fi2);
         return;
     }
     const bool neg = c0 < 0.0;
@@ -70,18 +79,33 @@ __device__ __forceinline__ void expi_coeffs(double c0, double c1, cplx<double> f
     }
 }
 
-__device__ __forceinline__ mat3<double> expi(const mat3<double>& Q) {
-    const mat3<double> Q2 = m_mul(Q, Q);
-    const double c1 = 0.5 * re_trace(Q2);
-    const double c0 = re_trace(m_mul(Q, Q2)) / 3.0;
+// exp(i Q) for Q Hermitian traceless given in the compact form (3 real diagonal, 3 complex upper entries):
+// Q^2 is Hermitian too, c1 = Tr Q^2 / 2 and c0 = det Q (= Tr Q^3 / 3) come from the entries directly
+__device__ __forceinline__ mat3<double> expi(const herm<double>& Q) {
+    const double d0 = Q.d[0], d1 = Q.d[1], d2 = Q.d[2];
+    const cplx<double> q01 = Q.o[0], q02 = Q.o[1], q12 = Q.o[2];
+    const double n01 = q01.re * q01.re + q01.im * q01.im;
+    const double n02 = q02.re * q02.re + q02.im * q02.im;
+    const double n12 = q12.re * q12.re + q12.im * q12.im;
+    herm<double> Q2;
+    Q2.d[0] = d0 * d0 + n01 + n02;
+    Q2.d[1] = d1 * d1 + n01 + n12;
+    Q2.d[2] = d2 * d2 + n02 + n12;
+    Q2.o[0] = cfma(q02, cconj(q12), cscale(q01, d0 + d1));   // Q01 (d0 + d1) + Q02 Q21
+    Q2.o[1] = cfma(q01, q12, cscale(q02, d0 + d2));          // Q02 (d0 + d2) + Q01 Q12
+    Q2.o[2] = cfma(cconj(q01), q02, cscale(q12, d1 + d2));   // Q12 (d1 + d2) + Q10 Q02
+    const double c1 = 0.5 * (Q2.d[0] + Q2.d[1] + Q2.d[2]);
+    const cplx<double> t = cmul(q01, q12);                   // Q01 Q12 Q20 = t conj(Q02)
+    const double c0 = d0 * d1 * d2 + 2.0 * (t.re * q02.re + t.im * q02.im) - d0 * n12 - d1 * n02 - d2 * n01;
     cplx<double> f[3];
     expi_coeffs(c0, c1, f);
+    const mat3<double> Qf = herm_full(Q), Q2f = herm_full(Q2);
     mat3<double> E;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            cplx<double> v = cadd(cmul(f[1], Q.e[i][j]), cmul(f[2], Q2.e[i][j]));
+            cplx<double> v = cadd(cmul(f[1], Qf.e[i][j]), cmul(f[2], Q2f.e[i][j]));
             if (i == j) v = cadd(v, f[0]);
             E.e[i][j] = v;
         }
@@ -134,8 +158,10 @@ __global__ void __launch_bounds__(kBlock) k_link_update(const double* __restrict
         load8(V + l * 8, v);
 #pragma unroll
         for (int a = 0; a < 8; a++) v[a] *= eps;
-        const mat3<double> Q = herm_full(coef_to_herm2(v));   // 2 eps V
-        const mat3<double> E = expi(m_scale(Q, 0.5));
+        herm<double> Q = coef_to_herm2(v);   // 2 eps V
+#pragma unroll
+        for (int k = 0; k < 3; k++) { Q.d[k] *= 0.5; Q.o[k] = cscale(Q.o[k], 0.5); }
+        const mat3<double> E = expi(Q);
         mat3<double> U;
         const double2* src = reinterpret_cast<const double2*>(Uin + l * 18);
 #pragma unroll

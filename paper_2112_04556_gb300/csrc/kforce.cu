@@ -96,6 +96,181 @@ int link_grad_launch(rmhmc_ctx* ctx, int prec, const void* X, const void* Z, int
 }
 
 // ------------------------------------------------------------------------------------------------
+// Kinetic force straight from the Krylov basis.  With X_j = sum_k cx_jk r_k and Z_j = sum_k cz_jk r_k on the
+// stored residuals r_k, the force on U = U_nu(y) is, in the adjoint representation R = Ad(U)
+// (U T^b U^dag = sum_c R_cb T^c) and with the su(3) structure constants f,
+//   G^a = (1/16) sum_cd f_acd (R C)_cd,   C = sum_mu sum_kl S_kl r_k,mu(y+nu) r_l,mu(y)^T,
+//   S_kl = sum_j alpha_j (cx_jk cz_jl + cz_jk cx_jl),
+// because coef_a(W Z - X W') = (1/2) f_acd [R (x' z^T + z' x^T)]_cd for W = U X' U^dag, W' = U Z' U^dag
+// (x, z, x', z' the coefficient vectors of X(y), Z(y), X(y+nu), Z(y+nu)).  One pass over the n basis
+// vectors replaces forming the 2 npole fields X_j, Z_j and the per-pole conjugations: per site about
+// 8 n^2 + 256 n + 1400 FMA per link against 576 npole per link for the direct form.
+// ------------------------------------------------------------------------------------------------
+
+// G_a += sum_c f_acd rc_c for one column d (d a compile-time constant after unrolling)
+template <typename T>
+__device__ __forceinline__ void f_contract(int d, const T (&rc)[8], T (&G)[8]) {
+    constexpr int tr[9][3] = {{0, 1, 2}, {0, 3, 6}, {0, 4, 5}, {1, 3, 5}, {1, 4, 6},
+                              {2, 3, 4}, {2, 5, 6}, {3, 4, 7}, {5, 6, 7}};
+    constexpr double fv[9] = {1.0, 0.5, -0.5, 0.5, 0.5, 0.5, -0.5, 0.86602540378443864676, 0.86602540378443864676};
+#pragma unroll
+    for (int t = 0; t < 9; t++) {
+        const int i = tr[t][0], j = tr[t][1], k = tr[t][2];
+        const T v = (T)fv[t];
+        if (d == k) { G[i] = fma(v, rc[j], G[i]); G[j] = fma(-v, rc[i], G[j]); }
+        else if (d == j) { G[k] = fma(v, rc[i], G[k]); G[i] = fma(-v, rc[k], G[i]); }
+        else if (d == i) { G[j] = fma(v, rc[k], G[j]); G[k] = fma(-v, rc[j], G[k]); }
+    }
+}
+
+// eight values from shared memory (plain loads: the read-only global path does not apply to shared memory)
+__device__ __forceinline__ void lds8(const float* p, float* x) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+}
+__device__ __forceinline__ void lds8(const double* p, double* x) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const double2 v = reinterpret_cast<const double2*>(p)[i];
+        x[2 * i] = v.x; x[2 * i + 1] = v.y;
+    }
+}
+
+constexpr int kLgSites = 32;   // sites per block (4 lanes each)
+constexpr int kLgKC = 4;       // basis vectors per chunk of W
+constexpr int kLgPad = kLgKC * 32 + 4;
+
+// S_kl (row stride ld) from the basis rows of X_j (rows j) and Z_j (rows ns + j), row stride ldr;
+// n from flags[1] when flags is given
+__global__ void __launch_bounds__(256) k_pair_matrix(const double* __restrict__ rows, int ldr, int ns, PairWeights w,
+                                                     const int* __restrict__ flags, int n, double* __restrict__ S, int ld) {
+    if (flags) n = flags[1];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
+        const int k = idx / n, l = idx % n;
+        double s = 0.0;
+        for (int j = 0; j < ns; j++) {
+            const double* X = rows + (size_t)j * ldr;
+            const double* Z = rows + (size_t)(ns + j) * ldr;
+            s = fma(w.w[j], fma(X[k], Z[l], Z[k] * X[l]), s);
+        }
+        S[(size_t)k * ld + l] = s;
+    }
+}
+
+// one block: kLgSites sites x 4 lanes.  Per chunk of kLgKC basis vectors: lane (y, mu) forms
+// W_k,mu(y) = sum_l S_kl r_l,mu(y) into shared memory; then lane (y, nu) accumulates
+// C += sum_mu r_k,mu(y+nu) W_k,mu(y)^T.  Finally lane (y, nu) conjugates the columns of C by U_nu(y) and
+// contracts with f.  n from flags[1] when flags is given.
+template <typename T, int LF>
+__global__ void __launch_bounds__(kLgSites * 4) k_link_grad_krylov(Geom g, typename LinksOf<T>::type U, const T* __restrict__ R,
+                                                                   size_t fs, const int* __restrict__ flags, int n,
+                                                                   const double* __restrict__ S, int ld, double* __restrict__ G) {
+    __shared__ __align__(16) T Ws[kLgSites * kLgPad];
+    __shared__ T Ss[kLgKC * kBasisCap];
+    if (flags) n = flags[1];
+    const int sl = threadIdx.x >> 2, q = threadIdx.x & 3;
+    T* const wrow = Ws + sl * kLgPad;
+    for (int base = blockIdx.x * kLgSites; base < g.V; base += gridDim.x * kLgSites) {
+        const int y = base + sl;
+        const bool live = y < g.V;
+        int yn = 0;
+        if (live) {
+            int fwd[4], bwd[4];
+            neighbours(g, y, fwd, bwd);
+            yn = fwd[q];
+        }
+        T C[8][8];
+#pragma unroll
+        for (int b = 0; b < 8; b++)
+#pragma unroll
+            for (int d = 0; d < 8; d++) C[b][d] = T(0);
+        for (int k0 = 0; k0 < n; k0 += kLgKC) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < kLgKC * n; t += blockDim.x) {
+                const int kk = t / n, l = t - kk * n;
+                Ss[kk * kBasisCap + l] = k0 + kk < n ? (T)S[(size_t)(k0 + kk) * ld + l] : T(0);
+            }
+            __syncthreads();
+            T w[kLgKC][8];
+#pragma unroll
+            for (int kk = 0; kk < kLgKC; kk++)
+#pragma unroll
+                for (int a = 0; a < 8; a++) w[kk][a] = T(0);
+            if (live) {
+                for (int l = 0; l < n; l++) {
+                    T r[8];
+                    load8(R + (size_t)l * fs + (size_t)y * 32 + q * 8, r);
+#pragma unroll
+                    for (int kk = 0; kk < kLgKC; kk++) {
+                        const T s = Ss[kk * kBasisCap + l];
+#pragma unroll
+                        for (int a = 0; a < 8; a++) w[kk][a] = fma(s, r[a], w[kk][a]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < kLgKC; kk++) store8(wrow + kk * 32 + q * 8, w[kk]);
+            __syncthreads();
+            if (live) {
+                const int kc = min(kLgKC, n - k0);
+                for (int kk = 0; kk < kc; kk++) {
+                    const T* rk = R + (size_t)(k0 + kk) * fs + (size_t)yn * 32;
+#pragma unroll
+                    for (int mu = 0; mu < 4; mu++) {
+                        T rp[8], wv[8];
+                        load8(rk + mu * 8, rp);
+                        lds8(wrow + kk * 32 + mu * 8, wv);
+#pragma unroll
+                        for (int b = 0; b < 8; b++)
+#pragma unroll
+                            for (int d = 0; d < 8; d++) C[b][d] = fma(rp[b], wv[d], C[b][d]);
+                    }
+                }
+            }
+        }
+        if (live) {
+            const mat3<T> u = LinkLoad<T, LF>::load(U, y, q);
+            T Gk[8];
+#pragma unroll
+            for (int a = 0; a < 8; a++) Gk[a] = T(0);
+#pragma unroll
+            for (int d = 0; d < 8; d++) {
+                T col[8], rc[8];
+#pragma unroll
+                for (int b = 0; b < 8; b++) col[b] = C[b][d];
+                herm<T> E = h_zero<T>();
+                acc_uxud(E, u, coef_to_herm2(col));   // 2 sum_c (R C)_cd T^c
+                herm2_to_coef(E, rc);                  // (R C)_cd
+                f_contract(d, rc, Gk);
+            }
+            double* out = G + (size_t)y * 32 + q * 8;
+#pragma unroll
+            for (int a = 0; a < 8; a++) out[a] = (double)Gk[a] * (1.0 / 16.0);
+        }
+    }
+}
+
+// F_K from the basis rows (X_j rows 0..ns-1, Z_j rows ns..2ns-1, row stride ldr, device float64) of the
+// float32 basis R; n on the host, or read on the device from flags[1] when flags is given
+int link_grad_krylov_launch(rmhmc_ctx* ctx, const float* R, const double* rows, int ldr, int ns, const double* alpha,
+                            const int* flags, int n, double* F, cudaStream_t st) {
+    if (ns > kMaxPairs) return set_err(ctx, RMHMC_EINVAL, "at most %d poles", kMaxPairs);
+    int status = RMHMC_OK;
+    double* S = (double*)workspace(ctx, "kf_pairs", sizeof(double) * kBasisCap * kBasisCap, &status);
+    if (!S) return status;
+    PairWeights pw{};
+    for (int j = 0; j < ns; j++) pw.w[j] = alpha[j];
+    k_pair_matrix<<<ctx->num_sms / 4 > 1 ? ctx->num_sms / 4 : 1, 256, 0, st>>>(rows, ldr, ns, pw, flags, n, S, kBasisCap);
+    ++ctx->launches;
+    const int grid = capped_grid(ctx, (size_t)ctx->g.V * 4, kLgSites * 4);
+    k_link_grad_krylov<float, 18><<<grid, kLgSites * 4, 0, st>>>(ctx->g, links32(ctx), R, field_elems(ctx), flags, n, S,
+                                                                 kBasisCap, F);
+    ++ctx->launches;
+    RM_LAUNCH_CHECK(ctx);
+    return RMHMC_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
 // kinetic pieces from a single Krylov run on P
 // ------------------------------------------------------------------------------------------------
 template <typename T>
@@ -163,8 +338,20 @@ static int kinetic_t(rmhmc_ctx* ctx, const MassTerm& m, const T* P, const double
         double* o[1] = {Vel};
         RM_TRY((krylov_combine<T, double>(ctx, spec, o, st)));
     }
-    if (F) {
-        T* XZ = (T*)workspace(ctx, sizeof(T) == 4 ? "kf_xz32" : "kf_xz64", sizeof(T) * fs * 2 * ns, &status);
+    if (F && sizeof(T) == 4) {
+        // float32 basis: the force straight from the basis (rows of X_j and Z_j on the stored residuals)
+        double* rows = (double*)workspace(ctx, "kf_rows", sizeof(double) * (size_t)2 * ns * kBasisCap, &status);
+        if (!rows) return status;
+        std::vector<double> h((size_t)2 * ns * n, 0.0);
+        for (int j = 0; j < ns; j++) {
+            tri.to_basis(ys[j], h.data() + (size_t)j * n);
+            tri.to_basis(zs[j], h.data() + (size_t)(ns + j) * n);
+        }
+        RM_TRY(upload(ctx, rows, h.data(), sizeof(double) * h.size(), st));
+        RM_TRY(link_grad_krylov_launch(ctx, (const float*)krylov_basis<T>(ctx), rows, n, ns, m.alpha.data(), nullptr, n,
+                                       F, st));
+    } else if (F) {
+        T* XZ = (T*)workspace(ctx, "kf_xz64", sizeof(T) * fs * 2 * ns, &status);
         if (!XZ) return status;
         CombineSpec spec;
         spec.n = n;

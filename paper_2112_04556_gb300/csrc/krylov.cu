@@ -374,7 +374,6 @@ struct KWork {
 };
 // the stored basis holds at most kBasisCap residuals: longer runs stop there and the caller's
 // reliable-update loop continues from the true residual (a restart)
-constexpr int kBasisCap = 160;
 
 template <typename T>
 static int krylov_workspace(rmhmc_ctx* ctx, int maxit, KWork& w) {
@@ -946,7 +945,7 @@ struct KinGraphBufs {
     double* vals = nullptr;
     double* rows = nullptr;
     double* work = nullptr;
-    float* XZ = nullptr;
+    double* pairs = nullptr;
     int maxit = 0;
 };
 
@@ -960,8 +959,8 @@ static int kin_graph_bufs(rmhmc_ctx* ctx, int ns, int maxit, KinGraphBufs& b) {
     void* sc = workspace(ctx, "kg_scal", 64 + sizeof(double) * 4 * (size_t)(kBasisCap + 2), &status);
     b.rows = (double*)workspace(ctx, "kg_rows", sizeof(double) * kBasisCap * (size_t)(2 * ns + 1), &status);
     b.work = (double*)workspace(ctx, "kg_work", sizeof(double) * kBasisCap * (size_t)(3 * ns + 1), &status);
-    b.XZ = (float*)workspace(ctx, "kf_xz32", sizeof(float) * fs * 2 * ns, &status);
-    if (!b.P32 || !b.R || !b.q || !sc || !b.rows || !b.work || !b.XZ) return status;
+    b.pairs = (double*)workspace(ctx, "kf_pairs", sizeof(double) * kBasisCap * kBasisCap, &status);
+    if (!b.P32 || !b.R || !b.q || !sc || !b.rows || !b.work || !b.pairs) return status;
     b.flags = (int*)sc;
     b.vals = (double*)((char*)sc + 64);
     return RMHMC_OK;
@@ -1022,15 +1021,12 @@ int kinetic_enqueue(rmhmc_ctx* ctx, const MassTerm& m, const double* P, double t
     }
     k_lanczos_rows<<<1, 128, 0, st>>>(b.flags, b.vals, b.maxit, dm, b.rows, b.work, status); ++ctx->launches;
     const int grid = (int)((fs + kBlock - 1) / kBlock);
-    OutPtrs<float, float> ox{};
-    for (int j = 0; j < 2 * ns; j++) ox.p[j] = b.XZ + (size_t)j * fs;
-    k_combine_dev<float, float><<<grid, kBlock, 0, st>>>(b.R, fs, b.flags, b.rows, 2 * ns, ox); ++ctx->launches;
     OutPtrs<float, double> ov{};
     ov.p[0] = Vel;
     k_combine_dev<float, double><<<grid, kBlock, 0, st>>>(b.R, fs, b.flags, b.rows + (size_t)2 * ns * kBasisCap, 1, ov);
     ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
-    return link_grad_launch(ctx, RMHMC_FP32, b.XZ, b.XZ + (size_t)ns * fs, ns, m.alpha.data(), F, st);
+    return link_grad_krylov_launch(ctx, b.R, b.rows, kBasisCap, ns, m.alpha.data(), b.flags, 0, F, st);
 }
 
 }  // namespace rm

@@ -15,6 +15,9 @@
 
 namespace rm {
 
+// capacity of the stored basis (residual vectors of one run)
+constexpr int kBasisCap = 160;
+
 struct KrylovResult {
     int n = 0;                      // iterations
     int status = 0;                 // as KScal::done

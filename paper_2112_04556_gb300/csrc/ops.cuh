@@ -16,5 +16,10 @@ int action_launch(rmhmc_ctx* ctx, double beta, double c1, double* S, double* pla
 // G = sum_f w_f d<Z_f, A X_f>/dw (X, Z in the arithmetic precision, [nf][V][4][8]); G float64 [V][4][8]
 int link_grad_launch(rmhmc_ctx* ctx, int prec, const void* X, const void* Z, int nf, const double* w, double* G,
                      cudaStream_t st);
+// kinetic force G = sum_j alpha_j d<Z_j, A X_j>/dw straight from the float32 Krylov basis R (n vectors), with
+// X_j, Z_j given as rows of basis coefficients (rows j and ns + j, row stride ldr, device float64); n is
+// read on the device from flags[1] when flags is not null.  G float64 [V][4][8].
+int link_grad_krylov_launch(rmhmc_ctx* ctx, const float* R, const double* rows, int ldr, int ns, const double* alpha,
+                            const int* flags, int n, double* G, cudaStream_t st);
 
 }  // namespace rm
