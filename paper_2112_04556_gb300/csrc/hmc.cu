@@ -28,84 +28,91 @@ constexpr int kSlotMax = 60;
 // Small Q (c1 = Tr Q^2 / 2 < 1/4): the power series with Q^3 = c1 Q + c0 reducing every power.
 // Otherwise: the closed form of Morningstar & Peardon, Phys. Rev. D 69 (2004) 054501.
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ void expi_coeffs(double c0, double c1, cplx<double> f[3]) {
-    if (c1 < 0.25) {
+// series cut-off per real type: a term below it no longer changes the sum
+template <typename T> struct ExpiCut;
+template <> struct ExpiCut<double> { static constexpr double v = 1e-18; };
+template <> struct ExpiCut<float> { static constexpr float v = 1e-9f; };
+
+template <typename T>
+__device__ __forceinline__ void expi_coeffs(T c0, T c1, cplx<T> f[3]) {
+    if (c1 < T(0.25)) {
         // f_k = sum_n (i^n / n!) {a_n, b_n, c_n}_k with Q^n = a_n I + b_n Q + c_n Q^2.  The eigenvalues of
         // Q are below sqrt(4 c1 / 3) < 1 in modulus, so |a_n| + |b_n| + |c_n| bounds the size of Q^n and the
-        // sum stops once a term falls below 1e-18; 1/n! are compile-time constants (no division)
-        double fr0 = 0.0, fr1 = 0.0, fr2 = 0.0, fi0 = 0.0, fi1 = 0.0, fi2 = 0.0;
-        double a = 1.0, b = 0.0, c = 0.0;
-        double inv = 1.0;   // 1/n!
+        // sum stops once a term falls below the cut-off; 1/n! are compile-time constants (no division)
+        T fr0 = 0, fr1 = 0, fr2 = 0, fi0 = 0, fi1 = 0, fi2 = 0;
+        T a = 1, b = 0, c = 0;
+        T inv = 1;   // 1/n!
 #pragma unroll
         for (int n = 0; n < 26; n++) {
-            const double sa = inv * a, sb = inv * b, sc = inv * c;
+            const T sa = inv * a, sb = inv * b, sc = inv * c;
             switch (n & 3) {   // i^n = 1, i, -1, -i
                 case 0: fr0 += sa; fr1 += sb; fr2 += sc; break;
                 case 1: fi0 += sa; fi1 += sb; fi2 += sc; break;
                 case 2: fr0 -= sa; fr1 -= sb; fr2 -= sc; break;
                 default: fi0 -= sa; fi1 -= sb; fi2 -= sc; break;
             }
-            if (n >= 3 && (fabs(sa) + fabs(sb) + fabs(sc)) < 1e-18) break;
-            const double an = c0 * c, bn = fma(c1, c, a), cn = b;
+            if (n >= 3 && (fabs(sa) + fabs(sb) + fabs(sc)) < ExpiCut<T>::v) break;
+            const T an = c0 * c, bn = fma(c1, c, a), cn = b;
             a = an; b = bn; c = cn;
-            inv *= 1.0 / (double)(n + 1);
+            inv *= T(1.0 / (double)(n + 1));
         }
         f[0] = cmk(fr0, fi0); f[1] = cmk(fr1, fi1); f[2] = cmk(fr2, fi2);
         return;
     }
-    const bool neg = c0 < 0.0;
-    const double c0p = fabs(c0);
-    const double c0max = 2.0 * pow(c1 / 3.0, 1.5);
-    const double ratio = fmin(1.0, c0p / c0max);
-    const double theta = acos(ratio);
-    const double u = sqrt(c1 / 3.0) * cos(theta / 3.0);
-    const double w = sqrt(c1) * sin(theta / 3.0);
-    const double u2 = u * u, w2 = w * w;
-    const double xi0 = fabs(w) < 0.05 ? 1.0 - w2 / 6.0 * (1.0 - w2 / 20.0 * (1.0 - w2 / 42.0)) : sin(w) / w;
-    const double cw = cos(w);
-    const cplx<double> e2iu = cmk(cos(2.0 * u), sin(2.0 * u));
-    const cplx<double> emiu = cmk(cos(u), -sin(u));
-    const cplx<double> h0 = cadd(cscale(e2iu, u2 - w2), cmul(emiu, cmk(8.0 * u2 * cw, 2.0 * u * (3.0 * u2 + w2) * xi0)));
-    const cplx<double> h1 = csub(cscale(e2iu, 2.0 * u), cmul(emiu, cmk(2.0 * u * cw, -(3.0 * u2 - w2) * xi0)));
-    const cplx<double> h2 = csub(e2iu, cmul(emiu, cmk(cw, 3.0 * u * xi0)));
-    const double den = 1.0 / (9.0 * u2 - w2);
+    const bool neg = c0 < T(0);
+    const T c0p = fabs(c0);
+    const T c0max = T(2) * pow(c1 / T(3), T(1.5));
+    const T ratio = fmin(T(1), c0p / c0max);
+    const T theta = acos(ratio);
+    const T u = sqrt(c1 / T(3)) * cos(theta / T(3));
+    const T w = sqrt(c1) * sin(theta / T(3));
+    const T u2 = u * u, w2 = w * w;
+    const T xi0 = fabs(w) < T(0.05) ? T(1) - w2 / T(6) * (T(1) - w2 / T(20) * (T(1) - w2 / T(42))) : sin(w) / w;
+    const T cw = cos(w);
+    const cplx<T> e2iu = cmk(cos(T(2) * u), sin(T(2) * u));
+    const cplx<T> emiu = cmk(cos(u), -sin(u));
+    const cplx<T> h0 = cadd(cscale(e2iu, u2 - w2), cmul(emiu, cmk(T(8) * u2 * cw, T(2) * u * (T(3) * u2 + w2) * xi0)));
+    const cplx<T> h1 = csub(cscale(e2iu, T(2) * u), cmul(emiu, cmk(T(2) * u * cw, -(T(3) * u2 - w2) * xi0)));
+    const cplx<T> h2 = csub(e2iu, cmul(emiu, cmk(cw, T(3) * u * xi0)));
+    const T den = T(1) / (T(9) * u2 - w2);
     f[0] = cscale(h0, den);
     f[1] = cscale(h1, den);
     f[2] = cscale(h2, den);
     if (neg) {   // f_j(-c0) = (-1)^j conj(f_j(c0))
         f[0] = cconj(f[0]);
-        f[1] = cscale(cconj(f[1]), -1.0);
+        f[1] = cscale(cconj(f[1]), T(-1));
         f[2] = cconj(f[2]);
     }
 }
 
 // exp(i Q) for Q Hermitian traceless given in the compact form (3 real diagonal, 3 complex upper entries):
 // Q^2 is Hermitian too, c1 = Tr Q^2 / 2 and c0 = det Q (= Tr Q^3 / 3) come from the entries directly
-__device__ __forceinline__ mat3<double> expi(const herm<double>& Q) {
-    const double d0 = Q.d[0], d1 = Q.d[1], d2 = Q.d[2];
-    const cplx<double> q01 = Q.o[0], q02 = Q.o[1], q12 = Q.o[2];
-    const double n01 = q01.re * q01.re + q01.im * q01.im;
-    const double n02 = q02.re * q02.re + q02.im * q02.im;
-    const double n12 = q12.re * q12.re + q12.im * q12.im;
-    herm<double> Q2;
+template <typename T>
+__device__ __forceinline__ mat3<T> expi(const herm<T>& Q) {
+    const T d0 = Q.d[0], d1 = Q.d[1], d2 = Q.d[2];
+    const cplx<T> q01 = Q.o[0], q02 = Q.o[1], q12 = Q.o[2];
+    const T n01 = q01.re * q01.re + q01.im * q01.im;
+    const T n02 = q02.re * q02.re + q02.im * q02.im;
+    const T n12 = q12.re * q12.re + q12.im * q12.im;
+    herm<T> Q2;
     Q2.d[0] = d0 * d0 + n01 + n02;
     Q2.d[1] = d1 * d1 + n01 + n12;
     Q2.d[2] = d2 * d2 + n02 + n12;
     Q2.o[0] = cfma(q02, cconj(q12), cscale(q01, d0 + d1));   // Q01 (d0 + d1) + Q02 Q21
     Q2.o[1] = cfma(q01, q12, cscale(q02, d0 + d2));          // Q02 (d0 + d2) + Q01 Q12
     Q2.o[2] = cfma(cconj(q01), q02, cscale(q12, d1 + d2));   // Q12 (d1 + d2) + Q10 Q02
-    const double c1 = 0.5 * (Q2.d[0] + Q2.d[1] + Q2.d[2]);
-    const cplx<double> t = cmul(q01, q12);                   // Q01 Q12 Q20 = t conj(Q02)
-    const double c0 = d0 * d1 * d2 + 2.0 * (t.re * q02.re + t.im * q02.im) - d0 * n12 - d1 * n02 - d2 * n01;
-    cplx<double> f[3];
-    expi_coeffs(c0, c1, f);
-    const mat3<double> Qf = herm_full(Q), Q2f = herm_full(Q2);
-    mat3<double> E;
+    const T c1 = T(0.5) * (Q2.d[0] + Q2.d[1] + Q2.d[2]);
+    const cplx<T> t = cmul(q01, q12);                        // Q01 Q12 Q20 = t conj(Q02)
+    const T c0 = d0 * d1 * d2 + T(2) * (t.re * q02.re + t.im * q02.im) - d0 * n12 - d1 * n02 - d2 * n01;
+    cplx<T> f[3];
+    expi_coeffs<T>(c0, c1, f);
+    const mat3<T> Qf = herm_full(Q), Q2f = herm_full(Q2);
+    mat3<T> E;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            cplx<double> v = cadd(cmul(f[1], Qf.e[i][j]), cmul(f[2], Q2f.e[i][j]));
+            cplx<T> v = cadd(cmul(f[1], Qf.e[i][j]), cmul(f[2], Q2f.e[i][j]));
             if (i == j) v = cadd(v, f[0]);
             E.e[i][j] = v;
         }
@@ -161,7 +168,7 @@ __global__ void __launch_bounds__(kBlock) k_link_update(const double* __restrict
         herm<double> Q = coef_to_herm2(v);   // 2 eps V
 #pragma unroll
         for (int k = 0; k < 3; k++) { Q.d[k] *= 0.5; Q.o[k] = cscale(Q.o[k], 0.5); }
-        const mat3<double> E = expi(Q);
+        const mat3<double> E = expi<double>(Q);
         mat3<double> U;
         const double2* src = reinterpret_cast<const double2*>(Uin + l * 18);
 #pragma unroll
@@ -202,6 +209,65 @@ __global__ void __launch_bounds__(kBlock) k_link_update(const double* __restrict
             double m = 0.0;
             for (int w = 0; w < kBlock / 32; w++) m = fmax(m, sh[w]);
             atomic_max_nonneg(maxdiff, m);
+        }
+    }
+}
+
+// One iterate of the link fixed point of the mixed-precision MD: W = exp(i eps V) B in float32 (B and V
+// float64, rounded on load).  Writes the float32 internal link copies (read by the float32 Krylov runs and
+// the float32 gauge force) and the compact iterate W32 [V][4][18] in place; with have_old, records
+// max |W_new - W_old| into *maxdiff.  Only the accepted iterate is recomputed in float64.
+__global__ void __launch_bounds__(kBlock) k_link_iter32(const double* __restrict__ B, const double* __restrict__ V,
+                                                        float eps, float* __restrict__ W32, int have_old,
+                                                        double* maxdiff, float4* u32a, float2* u32b, int nsite) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int mu = blockIdx.y;
+    float diff = 0.f;
+    if (s < nsite) {
+        const size_t l = (size_t)s * 4 + mu;
+        double vd[8];
+        load8(V + l * 8, vd);
+        float v[8];
+#pragma unroll
+        for (int a = 0; a < 8; a++) v[a] = (float)vd[a] * eps;
+        herm<float> Q = coef_to_herm2(v);   // 2 eps V
+#pragma unroll
+        for (int k = 0; k < 3; k++) { Q.d[k] *= 0.5f; Q.o[k] = cscale(Q.o[k], 0.5f); }
+        const mat3<float> E = expi<float>(Q);
+        mat3<float> Bf;
+        const double2* src = reinterpret_cast<const double2*>(B + l * 18);
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) { const double2 z = src[3 * i + j]; Bf.e[i][j] = cmk((float)z.x, (float)z.y); }
+        const mat3<float> R = m_mul(E, Bf);
+        float2* w = reinterpret_cast<float2*>(W32 + l * 18);
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                if (have_old) {
+                    const float2 o = w[3 * i + j];
+                    diff = fmaxf(diff, fmaxf(fabsf(R.e[i][j].re - o.x), fabsf(R.e[i][j].im - o.y)));
+                }
+                w[3 * i + j] = make_float2(R.e[i][j].re, R.e[i][j].im);
+            }
+        u32a[(size_t)(mu * 3 + 0) * nsite + s] = make_float4(R.e[0][0].re, R.e[0][0].im, R.e[0][1].re, R.e[0][1].im);
+        u32a[(size_t)(mu * 3 + 1) * nsite + s] = make_float4(R.e[0][2].re, R.e[0][2].im, R.e[1][0].re, R.e[1][0].im);
+        u32a[(size_t)(mu * 3 + 2) * nsite + s] = make_float4(R.e[1][1].re, R.e[1][1].im, R.e[1][2].re, R.e[1][2].im);
+#pragma unroll
+        for (int j = 0; j < 3; j++) u32b[(size_t)(mu * 3 + j) * nsite + s] = make_float2(R.e[2][j].re, R.e[2][j].im);
+    }
+    if (maxdiff) {
+        __shared__ float sh[kBlock / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) diff = fmaxf(diff, __shfl_down_sync(0xffffffffu, diff, o));
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = diff;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = 0.f;
+            for (int k = 0; k < kBlock / 32; k++) m = fmaxf(m, sh[k]);
+            atomic_max_nonneg(maxdiff, (double)m);
         }
     }
 }
@@ -258,6 +324,20 @@ static int link_update_launch(rmhmc_ctx* ctx, const double* Uin, const double* V
     return RMHMC_OK;
 }
 
+// float32 iterates of the link fixed point need a tolerance above float32 resolution of the O(1) link
+// entries (their rounding noise is ~1e-7); tighter tolerances iterate in float64
+constexpr double kIter32MinTol = 1e-6;
+static bool link_iterates_fp32(const rmhmc_params* p) { return p->prec != RMHMC_FP64 && p->fp_tol >= kIter32MinTol; }
+
+static int link_iter32_launch(rmhmc_ctx* ctx, const double* B, const double* V, double eps, float* W32, bool have_old,
+                              double* dmax, cudaStream_t st) {
+    const dim3 grid(site_blocks(ctx), 4);
+    k_link_iter32<<<grid, kBlock, 0, st>>>(B, V, (float)eps, W32, have_old ? 1 : 0, dmax, ctx->u32a, ctx->u32b, ctx->g.V);
+    ++ctx->launches;
+    RM_LAUNCH_CHECK(ctx);
+    return RMHMC_OK;
+}
+
 static int mom_update(rmhmc_ctx* ctx, const double* P, double h, const double* F1, const double* F2, const double* Qold,
                       double* Qn, double* dmax, cudaStream_t st) {
     const size_t n = field_elems(ctx);
@@ -269,6 +349,7 @@ static int mom_update(rmhmc_ctx* ctx, const double* P, double h, const double* F
 
 struct MDWork {
     double *FG, *FK, *V0, *Q, *B, *W, *dmax;
+    float* W32;   // float32 iterate of the link fixed point (mixed precision)
 };
 
 static int md_work(rmhmc_ctx* ctx, MDWork& w) {
@@ -281,7 +362,8 @@ static int md_work(rmhmc_ctx* ctx, MDWork& w) {
     w.B = (double*)workspace(ctx, "md_b", sizeof(double) * ls, &status);
     w.W = (double*)workspace(ctx, "md_w", sizeof(double) * ls, &status);
     w.dmax = (double*)workspace(ctx, "md_dmax", 64, &status);
-    if (!w.FG || !w.FK || !w.V0 || !w.Q || !w.B || !w.W || !w.dmax) return status;
+    w.W32 = (float*)workspace(ctx, "md_w32", sizeof(float) * (size_t)ctx->g.V * 72, &status);
+    if (!w.FG || !w.FK || !w.V0 || !w.Q || !w.B || !w.W || !w.dmax || !w.W32) return status;
     return RMHMC_OK;
 }
 
@@ -330,9 +412,14 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
             if (d <= p->fp_tol) { conv = true; worst = std::max(worst, d); break; }
         }
         if (!conv) return set_err(ctx, RMHMC_ENOCONV, "momentum fixed point: no convergence in %d iterations", p->fp_maxit);
-        // (2) link fixed point: B = exp(i eps/2 V0) U ; W = exp(i eps V0) U ; W <- exp(i eps/2 V(W)) B
+        // (2) link fixed point: B = exp(i eps/2 V0) U ; W = exp(i eps V0) U ; W <- exp(i eps/2 V(W)) B.
+        // float64: every iterate in float64.  Mixed (fp_tol >= 1e-6): the iterates (which only feed the
+        // float32 Krylov runs and the convergence test) in float32; the accepted one,
+        // exp(i eps/2 V(W_i)) B, in float64.
+        const bool it32 = link_iterates_fp32(p);
         RM_TRY(link_update_launch(ctx, U, w.V0, 0.5 * eps, false, w.B, nullptr, nullptr, false, st));
-        RM_TRY(link_update_launch(ctx, U, w.V0, eps, false, w.W, nullptr, nullptr, true, st));
+        if (it32) RM_TRY(link_iter32_launch(ctx, U, w.V0, eps, w.W32, false, nullptr, st));
+        else RM_TRY(link_update_launch(ctx, U, w.V0, eps, false, w.W, nullptr, nullptr, true, st));
         conv = false;
         for (int i = 0; i < p->fp_maxit; i++) {
             int it = 0;
@@ -340,18 +427,20 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
             solves++;
             kiters += it;
             RM_CHECK(ctx, cudaMemsetAsync(w.dmax, 0, sizeof(double), st));
-            // W_{i+1} into U's buffer (U is no longer needed: B holds exp(i eps/2 V0) U), then swap roles
-            RM_TRY(link_update_launch(ctx, w.B, w.V0, 0.5 * eps, false, U, w.W, w.dmax, true, st));
+            // W_{i+1} (float64: into U's buffer, U is no longer needed as B holds exp(i eps/2 V0) U)
+            if (it32) RM_TRY(link_iter32_launch(ctx, w.B, w.V0, 0.5 * eps, w.W32, true, w.dmax, st));
+            else RM_TRY(link_update_launch(ctx, w.B, w.V0, 0.5 * eps, false, U, w.W, w.dmax, true, st));
             double d = 0.0;
             RM_TRY(read_max(ctx, w.dmax, &d, st));
             fp_u++;
             if (!isfinite(d)) return set_err(ctx, RMHMC_ENAN, "NaN/Inf in the link fixed point");
-            RM_CHECK(ctx, cudaMemcpyAsync(w.W, U, lb, cudaMemcpyDeviceToDevice, st));
+            if (!it32) RM_CHECK(ctx, cudaMemcpyAsync(w.W, U, lb, cudaMemcpyDeviceToDevice, st));
             if (d <= p->fp_tol) { conv = true; worst = std::max(worst, d); break; }
         }
         if (!conv) return set_err(ctx, RMHMC_ENOCONV, "link fixed point: no convergence in %d iterations", p->fp_maxit);
-        // reunitarise the accepted links (in place) and refresh the internal copies
-        RM_TRY(link_update_launch(ctx, w.W, w.V0, 0.0, true, U, nullptr, nullptr, true, st));
+        // the accepted links, reunitarised, with fresh internal copies
+        if (it32) RM_TRY(link_update_launch(ctx, w.B, w.V0, 0.5 * eps, true, U, nullptr, nullptr, true, st));
+        else RM_TRY(link_update_launch(ctx, w.W, w.V0, 0.0, true, U, nullptr, nullptr, true, st));
         // (3) explicit half step with F_K(W_i, P') kept from the last iteration
         RM_TRY(gauge_force_launch(ctx, p->beta, p->c1, gprec, w.FG, st));
         RM_TRY(mom_update(ctx, w.Q, 0.5 * eps, w.FG, w.FK, nullptr, P, nullptr, st));
@@ -452,9 +541,12 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
                 if (cudaStreamEndCapture(aux, &tmp) != cudaSuccess && s == RMHMC_OK) s = RMHMC_ECUDA;
             }
             if (s != RMHMC_OK) break;
-            // (2) link fixed point
+            // (2) link fixed point (float32 iterates and the accepted one in float64, or float64 iterates)
+            const bool it32 = link_iterates_fp32(p);
             if ((s = link_update_launch(ctx, gb.U, w.V0, 0.5 * eps, false, w.B, nullptr, nullptr, false, st)) != RMHMC_OK) break;
-            if ((s = link_update_launch(ctx, gb.U, w.V0, eps, false, w.W, nullptr, nullptr, true, st)) != RMHMC_OK) break;
+            if (it32) s = link_iter32_launch(ctx, gb.U, w.V0, eps, w.W32, false, nullptr, st);
+            else s = link_update_launch(ctx, gb.U, w.V0, eps, false, w.W, nullptr, nullptr, true, st);
+            if (s != RMHMC_OK) break;
             if (cudaMemsetAsync(w.dmax, 0, sizeof(double), st) != cudaSuccess ||
                 cudaMemsetAsync(gb.ints + 1, 0, sizeof(int), st) != cudaSuccess) { s = RMHMC_ECUDA; break; }
             cudaGraphConditionalHandle h2;
@@ -466,8 +558,12 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
             }
             const size_t lb = sizeof(double) * (size_t)ctx->g.V * 72;
             s = kinetic_enqueue(ctx, m, w.Q, p->tol_md, p->maxiter, w.FK, w.V0, gb.stats, gb.ints, aux, aux2);
-            if (s == RMHMC_OK) s = link_update_launch(ctx, w.B, w.V0, 0.5 * eps, false, gb.U, w.W, w.dmax, true, aux);
-            if (s == RMHMC_OK && cudaMemcpyAsync(w.W, gb.U, lb, cudaMemcpyDeviceToDevice, aux) != cudaSuccess) s = RMHMC_ECUDA;
+            if (s == RMHMC_OK && it32) s = link_iter32_launch(ctx, w.B, w.V0, 0.5 * eps, w.W32, true, w.dmax, aux);
+            if (s == RMHMC_OK && !it32) {
+                s = link_update_launch(ctx, w.B, w.V0, 0.5 * eps, false, gb.U, w.W, w.dmax, true, aux);
+                if (s == RMHMC_OK && cudaMemcpyAsync(w.W, gb.U, lb, cudaMemcpyDeviceToDevice, aux) != cudaSuccess)
+                    s = RMHMC_ECUDA;
+            }
             if (s == RMHMC_OK) {
                 k_fp_decide<<<1, 32, 0, aux>>>(w.dmax, gb.ints + 1, p->fp_maxit, p->fp_tol, h2, gb.stats + 2, gb.ints);
                 ++ctx->launches;
@@ -477,8 +573,10 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
                 if (cudaStreamEndCapture(aux, &tmp) != cudaSuccess && s == RMHMC_OK) s = RMHMC_ECUDA;
             }
             if (s != RMHMC_OK) break;
-            // reunitarise, (3) explicit half step, next initial guess
-            if ((s = link_update_launch(ctx, w.W, w.V0, 0.0, true, gb.U, nullptr, nullptr, true, st)) != RMHMC_OK) break;
+            // the accepted links in float64, reunitarised; (3) explicit half step, next initial guess
+            if (it32) s = link_update_launch(ctx, w.B, w.V0, 0.5 * eps, true, gb.U, nullptr, nullptr, true, st);
+            else s = link_update_launch(ctx, w.W, w.V0, 0.0, true, gb.U, nullptr, nullptr, true, st);
+            if (s != RMHMC_OK) break;
             if ((s = gauge_force_launch(ctx, p->beta, p->c1, gprec, w.FG, st)) != RMHMC_OK) break;
             if ((s = mom_update(ctx, w.Q, 0.5 * eps, w.FG, w.FK, nullptr, gb.P, nullptr, st)) != RMHMC_OK) break;
             if ((s = mom_update(ctx, gb.P, 0.5 * eps, w.FG, w.FK, nullptr, w.Q, nullptr, st)) != RMHMC_OK) break;

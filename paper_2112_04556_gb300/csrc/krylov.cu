@@ -12,7 +12,6 @@
 
 namespace rm {
 
-constexpr int kSlotGamma = 0, kSlotRho = 1, kSlotNorm = 2, kSlotResid = 8;   // reduction slots
 constexpr int kCheckChunk = 8;                                                 // iterations per flag check
 constexpr int kMaxCombine = 32;                                                // outputs per combine launch
 
@@ -617,15 +616,20 @@ int solve_shifts(rmhmc_ctx* ctx, const MassTerm& m, const double* b, double tol,
             // fall through to the refinement check, which reports ENOCONV if needed
         }
     }
-    // reliable updates: float64 true residuals, corrections per shift
-    double* r = (double*)workspace(ctx, "ss_r", sizeof(double) * fs * ns, &status);
-    float* r32 = mixed ? (float*)workspace(ctx, "ss_r32", sizeof(float) * fs, &status) : nullptr;
+    // reliable updates: true residuals to float64 accuracy, corrections per shift.  Mixed precision
+    // forms them from float32 arithmetic with compensated sums (resid_df.cu) on the adjoint table of
+    // the links, which stay fixed for the whole solve.
+    double* r = !mixed ? (double*)workspace(ctx, "ss_r", sizeof(double) * fs * ns, &status) : nullptr;
+    float* r32 = mixed ? (float*)workspace(ctx, "ss_r32", sizeof(float) * fs * ns, &status) : nullptr;
     float* e32 = mixed ? (float*)workspace(ctx, "ss_e32", sizeof(float) * fs, &status) : nullptr;
     double* e64 = !mixed ? (double*)workspace(ctx, "ss_e64", sizeof(double) * fs, &status) : nullptr;
-    if (!r || (mixed && (!r32 || !e32)) || (!mixed && !e64)) return status;
+    if ((mixed && (!r32 || !e32)) || (!mixed && (!r || !e64))) return status;
+    float* adj = nullptr;
+    if (mixed) RM_TRY(adjoint_table(ctx, &adj, st));
     std::vector<double> n2(ns);
     for (int cycle = 0;; cycle++) {
-        RM_TRY(resid64(ctx, b, xs, ns, m.sigma.data(), r, n2.data(), st));
+        if (mixed) RM_TRY(resid_df(ctx, adj, b, xs, ns, m.sigma.data(), r32, n2.data(), st));
+        else RM_TRY(resid64(ctx, b, xs, ns, m.sigma.data(), r, n2.data(), st));
         bool all = true;
         for (int j = 0; j < ns; j++) {
             const double rel = sqrt(n2[j] / b2);
@@ -641,12 +645,11 @@ int solve_shifts(rmhmc_ctx* ctx, const MassTerm& m, const double* b, double tol,
             if (rel <= tol) continue;
             const double want = std::max(0.5 * tol / rel, 1e-15);
             KrylovResult kr;
-            const double* rj = r + (size_t)j * fs;
             if (mixed) {
-                RM_TRY(to_float(ctx, rj, r32, fs, st));
-                RM_TRY(krylov_run<float>(ctx, r32, m.sigma[j], std::max(want, floor32), maxiter, kr, st));
+                RM_TRY(krylov_run<float>(ctx, r32 + (size_t)j * fs, m.sigma[j], std::max(want, floor32), maxiter, kr,
+                                         st));
             } else {
-                RM_TRY(krylov_run<double>(ctx, rj, m.sigma[j], want, maxiter, kr, st));
+                RM_TRY(krylov_run<double>(ctx, r + (size_t)j * fs, m.sigma[j], want, maxiter, kr, st));
             }
             total += kr.n;
             Tridiag tri;

@@ -17,6 +17,8 @@ namespace rm {
 
 // capacity of the stored basis (residual vectors of one run)
 constexpr int kBasisCap = 160;
+// reduction slots of the Krylov engine (the residual norms use kSlotResid .. kSlotResid + nshift - 1)
+constexpr int kSlotGamma = 0, kSlotRho = 1, kSlotNorm = 2, kSlotResid = 8;
 
 struct KrylovResult {
     int n = 0;                      // iterations
@@ -57,6 +59,12 @@ int krylov_combine(rmhmc_ctx* ctx, const CombineSpec& spec, TO* const* outs, cud
 // norms to host norm2[nf]; r (nullable) stores the residual fields
 int resid64(rmhmc_ctx* ctx, const double* b, const double* x, int nf, const double* sigma, double* r, double* norm2,
             cudaStream_t st);
+
+// the same residuals from float32 arithmetic with compensated (float32-pair) sums: tab is the adjoint table
+// of the context's links (adjoint_table), r receives the residuals rounded to float32 ([nf][V][4][8])
+int adjoint_table(rmhmc_ctx* ctx, float** tab, cudaStream_t st);
+int resid_df(rmhmc_ctx* ctx, const float* tab, const double* b, const double* x, int nf, const double* sigma, float* r,
+             double* norm2, cudaStream_t st);
 
 // float64 -> float32 field conversion and float32 correction accumulation
 int to_float(rmhmc_ctx* ctx, const double* in, float* out, size_t n, cudaStream_t st);

@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("L", [(4, 4, 4, 4), (5, 3, 4, 7)])
-@pytest.mark.parametrize("prec,tol,bound", [(0, 1e-12, 1e-11), (1, 1e-10, 1e-9)])
+@pytest.mark.parametrize("prec,tol,bound", [(0, 1e-12, 1e-11), (1, 1e-10, 1e-9), (1, 1e-12, 1e-11)])
 def test_rat_mass_solve_parity(L, prec, tol, bound):
     import paper_2112_04556_gb300 as rm
     U = inputs.random_links(L, eps=0.5, seed=21)
