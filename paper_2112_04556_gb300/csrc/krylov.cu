@@ -190,52 +190,80 @@ __global__ void __launch_bounds__(kBlock) k_cg_B(T* __restrict__ R, size_t fs, c
     }
 }
 
-// out[m] = sum_k coef[m][k] basis_k; one real per thread (coalesced), coefficients staged through shared
-// memory, eight basis vectors in flight per step
+// out[m] = sum_{k < n} coef[m][k] basis_k for m < M <= MB.  Every coefficient is staged in shared memory
+// once per block; the grid strides over vectors of 16 bytes (float4 / double2) so every basis vector is
+// read with 128-bit loads, four vectors in flight per step.  n is read from flags[1] when flags is given
+// (device-decided Krylov length); coefficient row stride ldc.
 template <typename T, typename TO>
 struct OutPtrs { TO* p[kMaxCombine]; };
 
-template <typename T, typename TO>
-__global__ void __launch_bounds__(kBlock) k_combine(const T* __restrict__ R, size_t fs, int n, const double* __restrict__ coef,
-                                                     int M, OutPtrs<T, TO> outs) {
-    constexpr int KC = 64, UN = 8;
-    __shared__ T cs[kMaxCombine * KC];
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    T acc[kMaxCombine];
-#pragma unroll
-    for (int m = 0; m < kMaxCombine; m++) acc[m] = T(0);
-    for (int k0 = 0; k0 < n; k0 += KC) {
-        const int kc = min(KC, n - k0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < M * kc; t += blockDim.x) {
-            const int m = t / kc, kk = t % kc;
-            cs[m * KC + kk] = (T)coef[(size_t)m * n + k0 + kk];
-        }
-        __syncthreads();
-        if (i < fs) {
-            int kk = 0;
-            for (; kk + UN <= kc; kk += UN) {
-                T x[UN];
-#pragma unroll
-                for (int u = 0; u < UN; u++) x[u] = __ldg(R + (size_t)(k0 + kk + u) * fs + i);
-#pragma unroll
-                for (int u = 0; u < UN; u++)
-#pragma unroll
-                    for (int m = 0; m < kMaxCombine; m++)
-                        if (m < M) acc[m] = fma(cs[m * KC + kk + u], x[u], acc[m]);
-            }
-            for (; kk < kc; kk++) {
-                const T x = __ldg(R + (size_t)(k0 + kk) * fs + i);
-#pragma unroll
-                for (int m = 0; m < kMaxCombine; m++)
-                    if (m < M) acc[m] = fma(cs[m * KC + kk], x, acc[m]);
-            }
-        }
+template <typename T> __device__ __forceinline__ void store_vec(T* p, const T* x);
+template <> __device__ __forceinline__ void store_vec<float>(float* p, const float* x) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+}
+template <> __device__ __forceinline__ void store_vec<double>(double* p, const double* x) {
+    *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
+}
+
+template <typename T, typename TO, int MB>
+__global__ void __launch_bounds__(kBlock) k_combine(const T* __restrict__ R, size_t fs, const int* __restrict__ flags, int n,
+                                                     const double* __restrict__ coef, int ldc, int M, OutPtrs<T, TO> outs) {
+    using VT = Vec<T>;
+    constexpr int VN = VT::n, UN = 4;
+    __shared__ T cs[MB * kBasisCap];
+    if (flags) n = flags[1];
+    for (int t = threadIdx.x; t < M * n; t += blockDim.x) {
+        const int m = t / n, k = t - m * n;
+        cs[m * kBasisCap + k] = (T)coef[(size_t)m * ldc + k];
     }
-    if (i < fs) {
+    __syncthreads();
+    const size_t nvec = fs / VN;
+    const typename VT::type* Rv = reinterpret_cast<const typename VT::type*>(R);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvec; i += (size_t)gridDim.x * blockDim.x) {
+        T acc[MB][VN];
 #pragma unroll
-        for (int m = 0; m < kMaxCombine; m++)
-            if (m < M) outs.p[m][i] = (TO)acc[m];
+        for (int m = 0; m < MB; m++)
+#pragma unroll
+            for (int v = 0; v < VN; v++) acc[m][v] = T(0);
+        int k = 0;
+        for (; k + UN <= n; k += UN) {
+            T x[UN][VN];
+#pragma unroll
+            for (int u = 0; u < UN; u++) VT::get(__ldg(Rv + (size_t)(k + u) * nvec + i), x[u]);
+#pragma unroll
+            for (int u = 0; u < UN; u++)
+#pragma unroll
+                for (int m = 0; m < MB; m++)
+                    if (m < M) {
+                        const T c = cs[m * kBasisCap + k + u];
+#pragma unroll
+                        for (int v = 0; v < VN; v++) acc[m][v] = fma(c, x[u][v], acc[m][v]);
+                    }
+        }
+        for (; k < n; k++) {
+            T x[VN];
+            VT::get(__ldg(Rv + (size_t)k * nvec + i), x);
+#pragma unroll
+            for (int m = 0; m < MB; m++)
+                if (m < M) {
+                    const T c = cs[m * kBasisCap + k];
+#pragma unroll
+                    for (int v = 0; v < VN; v++) acc[m][v] = fma(c, x[v], acc[m][v]);
+                }
+        }
+#pragma unroll
+        for (int m = 0; m < MB; m++)
+            if (m < M) {
+                TO o[VN];
+#pragma unroll
+                for (int v = 0; v < VN; v++) o[v] = (TO)acc[m][v];
+                TO* dst = outs.p[m] + i * VN;
+                if (sizeof(TO) == sizeof(T)) store_vec<TO>(dst, o);
+                else {
+#pragma unroll
+                    for (int v = 0; v < VN; v += 16 / (int)sizeof(TO)) store_vec<TO>(dst + v, o + v);
+                }
+            }
     }
 }
 
@@ -495,15 +523,20 @@ int krylov_combine(rmhmc_ctx* ctx, const CombineSpec& spec, TO* const* outs, cud
     int status = RMHMC_OK;
     const T* R = krylov_basis<T>(ctx);
     const size_t fs = field_elems(ctx);
-    for (int m0 = 0; m0 < spec.M; m0 += kMaxCombine) {
-        const int mc = std::min(kMaxCombine, spec.M - m0);
-        double* dcoef = (double*)workspace(ctx, "kr_coef", sizeof(double) * (size_t)kMaxCombine * kBasisCap, &status);
-        if (!dcoef) return status;
-        RM_TRY(upload(ctx, dcoef, spec.coef.data() + (size_t)m0 * spec.n, sizeof(double) * (size_t)mc * spec.n, st));
+    constexpr int kChunk = 12;   // outputs per launch (accumulators per thread: 12 x one 16-byte vector)
+    const size_t ncoef = std::max((size_t)kMaxCombine * kBasisCap, (size_t)spec.M * spec.n);
+    double* dcoef = (double*)workspace(ctx, "kr_coef", sizeof(double) * ncoef, &status);
+    if (!dcoef) return status;
+    RM_TRY(upload(ctx, dcoef, spec.coef.data(), sizeof(double) * (size_t)spec.M * spec.n, st));
+    const int grid = capped_grid(ctx, fs / Vec<T>::n, kBlock);
+    for (int m0 = 0; m0 < spec.M; m0 += kChunk) {
+        const int mc = std::min(kChunk, spec.M - m0);
         OutPtrs<T, TO> op{};
         for (int m = 0; m < mc; m++) op.p[m] = outs[m0 + m];
-        const int grid = (int)((fs + kBlock - 1) / kBlock);
-        k_combine<T, TO><<<grid, kBlock, 0, st>>>(R, fs, spec.n, dcoef, mc, op); ++ctx->launches;
+        const double* c = dcoef + (size_t)m0 * spec.n;
+        if (mc == 1) k_combine<T, TO, 1><<<grid, kBlock, 0, st>>>(R, fs, nullptr, spec.n, c, spec.n, 1, op);
+        else k_combine<T, TO, kChunk><<<grid, kBlock, 0, st>>>(R, fs, nullptr, spec.n, c, spec.n, mc, op);
+        ++ctx->launches;
         RM_LAUNCH_CHECK(ctx);
     }
     return RMHMC_OK;
@@ -861,52 +894,6 @@ __global__ void __launch_bounds__(128) k_lanczos_rows(const int* __restrict__ fl
     }
 }
 
-// out[m] = sum_{k < n} rows[m][k] basis_k with n read on the device; row stride kBasisCap
-template <typename T, typename TO>
-__global__ void __launch_bounds__(kBlock) k_combine_dev(const T* __restrict__ R, size_t fs, const int* __restrict__ flags,
-                                                        const double* __restrict__ rows, int M, OutPtrs<T, TO> outs) {
-    constexpr int KC = 64, UN = 8;
-    __shared__ T cs[kMaxCombine * KC];
-    const int n = flags[1];
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    T acc[kMaxCombine];
-#pragma unroll
-    for (int m = 0; m < kMaxCombine; m++) acc[m] = T(0);
-    for (int k0 = 0; k0 < n; k0 += KC) {
-        const int kc = min(KC, n - k0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < M * kc; t += blockDim.x) {
-            const int m = t / kc, kk = t % kc;
-            cs[m * KC + kk] = (T)rows[(size_t)m * kBasisCap + k0 + kk];
-        }
-        __syncthreads();
-        if (i < fs) {
-            int kk = 0;
-            for (; kk + UN <= kc; kk += UN) {
-                T x[UN];
-#pragma unroll
-                for (int u = 0; u < UN; u++) x[u] = __ldg(R + (size_t)(k0 + kk + u) * fs + i);
-#pragma unroll
-                for (int u = 0; u < UN; u++)
-#pragma unroll
-                    for (int m = 0; m < kMaxCombine; m++)
-                        if (m < M) acc[m] = fma(cs[m * KC + kk + u], x[u], acc[m]);
-            }
-            for (; kk < kc; kk++) {
-                const T x = __ldg(R + (size_t)(k0 + kk) * fs + i);
-#pragma unroll
-                for (int m = 0; m < kMaxCombine; m++)
-                    if (m < M) acc[m] = fma(cs[m * KC + kk], x, acc[m]);
-            }
-        }
-    }
-    if (i < fs) {
-#pragma unroll
-        for (int m = 0; m < kMaxCombine; m++)
-            if (m < M) outs.p[m][i] = (TO)acc[m];
-    }
-}
-
 // handle of a conditional node in the graph that stream st is capturing into
 int capture_handle(rmhmc_ctx* ctx, cudaStream_t st, unsigned init, cudaGraphConditionalHandle* h) {
     cudaStreamCaptureStatus cs;
@@ -1023,10 +1010,11 @@ int kinetic_enqueue(rmhmc_ctx* ctx, const MassTerm& m, const double* P, double t
         RM_CHECK(ctx, cudaStreamEndCapture(aux, &tmp));
     }
     k_lanczos_rows<<<1, 128, 0, st>>>(b.flags, b.vals, b.maxit, dm, b.rows, b.work, status); ++ctx->launches;
-    const int grid = (int)((fs + kBlock - 1) / kBlock);
+    const int grid = capped_grid(ctx, fs / 4, kBlock);
     OutPtrs<float, double> ov{};
     ov.p[0] = Vel;
-    k_combine_dev<float, double><<<grid, kBlock, 0, st>>>(b.R, fs, b.flags, b.rows + (size_t)2 * ns * kBasisCap, 1, ov);
+    k_combine<float, double, 1><<<grid, kBlock, 0, st>>>(b.R, fs, b.flags, 0, b.rows + (size_t)2 * ns * kBasisCap,
+                                                         kBasisCap, 1, ov);
     ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     return link_grad_krylov_launch(ctx, b.R, b.rows, kBasisCap, ns, m.alpha.data(), b.flags, 0, F, st);
