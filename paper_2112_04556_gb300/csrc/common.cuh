@@ -154,6 +154,13 @@ __device__ __forceinline__ void load8(const float* p, float* x) {
     float4 a = __ldg(q), b = __ldg(q + 1);
     x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
 }
+// eight floats with one 256-bit read-only global load (sm_100 and later).  p must be 32-byte aligned and
+// the data must not change during the kernel: used on the context's own buffers only.
+__device__ __forceinline__ void load8_v8(const float* p, float* x) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
+        : "l"(p));
+}
 __device__ __forceinline__ void store8(double* p, const double* x) {
     double2* q = reinterpret_cast<double2*>(p);
 #pragma unroll

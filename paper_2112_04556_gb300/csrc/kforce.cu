@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) k_pair_matrix(const double* __restrict__ 
 // C += sum_mu r_k,mu(y+nu) W_k,mu(y)^T.  Finally lane (y, nu) conjugates the columns of C by U_nu(y) and
 // contracts with f.  n from flags[1] when flags is given.
 template <typename T, int LF>
-__global__ void __launch_bounds__(kLgSites * 4) k_link_grad_krylov(Geom g, typename LinksOf<T>::type U, const T* __restrict__ R,
+__global__ void __launch_bounds__(kLgSites * 4, 4) k_link_grad_krylov(Geom g, typename LinksOf<T>::type U, const T* __restrict__ R,
                                                                    size_t fs, const int* __restrict__ flags, int n,
                                                                    const double* __restrict__ S, int ld, double* __restrict__ G) {
     __shared__ __align__(16) T Ws[kLgSites * kLgPad];
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kLgSites * 4) k_link_grad_krylov(Geom g, typen
             if (live) {
                 for (int l = 0; l < n; l++) {
                     T r[8];
-                    load8(R + (size_t)l * fs + (size_t)y * 32 + q * 8, r);
+                    load8_v8(R + (size_t)l * fs + (size_t)y * 32 + q * 8, r);
 #pragma unroll
                     for (int kk = 0; kk < kLgKC; kk++) {
                         const T s = Ss[kk * kBasisCap + l];
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kLgSites * 4) k_link_grad_krylov(Geom g, typen
 #pragma unroll
                     for (int mu = 0; mu < 4; mu++) {
                         T rp[8], wv[8];
-                        load8(rk + mu * 8, rp);
+                        load8_v8(rk + mu * 8, rp);
                         lds8(wrow + kk * 32 + mu * 8, wv);
 #pragma unroll
                         for (int b = 0; b < 8; b++)

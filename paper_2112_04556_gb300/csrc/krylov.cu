@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_start(const T* __restrict__ b, T*
 // (p_k = r_k + beta_{k-1} p_{k-1}), so the stencil reads only r_k; gamma_k = <p_k, A p_k> = <r_k, q_k> by
 // A-conjugacy of the directions, alpha_k = rho_k / gamma_k.  q is updated in place at the lane's own site.
 template <typename T, int LF, int NMU>
-__global__ void __launch_bounds__(kBlockMax) k_cg_A(Geom g, typename LinksOf<T>::type U, const T* __restrict__ R, size_t fs,
+__global__ void __launch_bounds__(kBlockMax, (stencil_min_blocks<T, NMU>())) k_cg_A(Geom g, typename LinksOf<T>::type U, const T* __restrict__ R, size_t fs,
                                                      T* __restrict__ q, T diag, const int* __restrict__ flags,
                                                      double* vals, int maxit, double* partials, unsigned* counter) {
     constexpr int NC = NMU == 0 ? 1 : NMU;   // components per lane
@@ -83,13 +83,15 @@ __global__ void __launch_bounds__(kBlockMax) k_cg_A(Geom g, typename LinksOf<T>:
     for (int lane = blockIdx.x * blockDim.x + threadIdx.x; lane < nlane; lane += gridDim.x * blockDim.x) {
         const int s = lane / LPS, mu0 = (lane % LPS) * NC;
         herm<T> acc[NC];
-        hop_sum_shape<T, LF, NMU>(g, U, s, mu0, SrcField<T>{r}, acc);
+        if constexpr (sizeof(T) == 4 && NMU == 1) hop_sum_shape<T, LF, NMU>(g, U, s, mu0, SrcFieldV8{r}, acc);
+        else hop_sum_shape<T, LF, NMU>(g, U, s, mu0, SrcField<T>{r}, acc);
 #pragma unroll
         for (int m = 0; m < NC; m++) {
             const int mu = mu0 + m;
             T h[8], x[8], y[8];
             herm2_to_coef(acc[m], h);
-            load8(r + (size_t)s * 32 + mu * 8, x);
+            if constexpr (sizeof(T) == 4 && NMU == 1) load8_v8(r + (size_t)s * 32 + mu * 8, x);
+            else load8(r + (size_t)s * 32 + mu * 8, x);
             T* qs = q + (size_t)s * 32 + mu * 8;
             if (k > 0) {
                 load8(qs, y);

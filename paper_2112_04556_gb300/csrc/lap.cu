@@ -10,7 +10,7 @@
 namespace rm {
 
 template <typename T, int LF, int NMU, bool HAS_W, bool DOTS>
-__global__ void __launch_bounds__(kBlockMax) k_lap(Geom g, typename LinksOf<T>::type U, const T* __restrict__ X,
+__global__ void __launch_bounds__(kBlockMax, (stencil_min_blocks<T, NMU>())) k_lap(Geom g, typename LinksOf<T>::type U, const T* __restrict__ X,
                                                     T* __restrict__ Y, const T* __restrict__ W, T a, T b, T c,
                                                     size_t fstride, double* partials, unsigned* counters, double* out,
                                                     size_t slot_stride) {

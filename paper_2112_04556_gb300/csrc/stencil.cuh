@@ -93,6 +93,13 @@ template <typename T> struct SrcField {
     __device__ __forceinline__ void operator()(int s, int mu, T* x) const { load8(X + (size_t)s * 32 + mu * 8, x); }
 };
 
+// plain float32 field of the context's own (32-byte aligned, read-only during the kernel) buffers, read with
+// 256-bit loads
+struct SrcFieldV8 {
+    const float* X;
+    __device__ __forceinline__ void operator()(int s, int mu, float* x) const { load8_v8(X + (size_t)s * 32 + mu * 8, x); }
+};
+
 // fused source r + beta * p (conjugate-gradient search direction)
 template <typename T> struct SrcAxpy {
     const T* r;

@@ -14,6 +14,13 @@ struct StencilShape {
     int nmu = 1;
     int block = 128;
 };
+// minimum resident blocks of kBlockMax threads each stencil shape is compiled for (the register budget): the
+// float32 one-component shape fits 64 registers (4 blocks, 32 warps per SM), the two-component and
+// prefetching shapes 85 (3 blocks), the four-component shape 128 (2 blocks); float64 shapes are not bounded
+template <typename T, int NMU> constexpr int stencil_min_blocks() {
+    return sizeof(T) == 8 ? 1 : NMU == 1 ? 4 : NMU == 4 ? 2 : 3;
+}
+
 inline int lanes_per_site(int nmu) { return nmu == 0 ? 4 : 4 / nmu; }
 
 // shape for (sizeof(T), LF); tunes on first use
