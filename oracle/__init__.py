@@ -470,3 +470,34 @@ def plain_hmc(L, U, ntraj, beta, seed, tau=1.0, nsteps=20, c1=0.0, metropolis=Tr
         U = r["U"]
         acc += r["accepted"]
     return U, acc
+
+
+# --------------------------------------------------------------------------
+# Wilson gradient flow and the flowed energy (the observable of Sec. 4, defined by Luscher,
+# JHEP 08 (2010) 071, which the paper cites for it)
+# --------------------------------------------------------------------------
+
+def flow_energy(L, U):
+    """Plaquette definition of the energy density, averaged over sites:
+    E = (1/V) sum_x 2 sum_{mu<nu} Re Tr(1 - P_mu,nu(x)) = 36 (1 - <Re Tr P / 3>)."""
+    _, plaq = action(L, U, 1.0)
+    return 36.0 * (1.0 - plaq)
+
+
+def wilson_flow(L, U, eps, nsteps):
+    """Luscher's third-order Runge-Kutta scheme for dV/dt = -g0^2 (dS_W) V, nsteps steps of size eps:
+        W1 = exp(Z0/4) W0,  W2 = exp(8/9 Z1 - 17/36 Z0) W1,  W3 = exp(3/4 Z2 - 8/9 Z1 + 17/36 Z0) W2,
+    Z_i = eps Z(W_i).  With U -> exp(i w^a T^a) U and F = -dS/dw (gauge_force), the flow velocity is
+    i g0^2 F^a T^a; g0^2 = 6/beta and F is proportional to beta, so g0^2 F = 6 F(beta = 1) and the
+    flow does not depend on beta.  Returns the flowed links and E(t) at t = 0, eps, ..., nsteps eps."""
+    U = np.array(U, dtype=np.complex128, copy=True)
+    E = [flow_energy(L, U)]
+    for _ in range(nsteps):
+        Z0 = 6.0 * gauge_force(L, U, 1.0)
+        W1 = link_update(L, U, Z0, 0.25 * eps)
+        Z1 = 6.0 * gauge_force(L, W1, 1.0)
+        W2 = link_update(L, W1, (8.0 / 9.0) * Z1 - (17.0 / 36.0) * Z0, eps)
+        Z2 = 6.0 * gauge_force(L, W2, 1.0)
+        U = link_update(L, W2, 0.75 * Z2 - (8.0 / 9.0) * Z1 + (17.0 / 36.0) * Z0, eps)
+        E.append(flow_energy(L, U))
+    return U, np.array(E)
