@@ -310,6 +310,22 @@ def cheb_moments(L, U, F, N):
     return mu
 
 
+def cheb_filter_apply(L, U, F, coef):
+    """Y = sum_k coef[k] T_k(2A - 1) F: the filter applied as a vector (band-filtered fields of Sec. 4),
+    by the same plain three-term recurrence, accumulating every term."""
+    H = lambda v: 2.0 * lap(L, U, v) - v
+    N = len(coef) - 1
+    Y = coef[0] * F
+    if N == 0:
+        return Y
+    v_prev, v = F, H(F)
+    Y = Y + coef[1] * v
+    for k in range(2, N + 1):
+        v_prev, v = v, 2.0 * H(v) - v_prev
+        Y = Y + coef[k] * v
+    return Y
+
+
 def jackson(N):
     """Jackson damping g_k, k = 0..N (kernel polynomial method)."""
     k = np.arange(N + 1)

@@ -127,3 +127,37 @@ def test_spectrum_gauge_invariant(oracle_lib):
     s0 = oracle_lib.power_spectrum(L, U, [F], list(eta), 32, inputs.equal_windows(8))[0]
     s1 = oracle_lib.power_spectrum(L, Up, [Fp], etap, 32, inputs.equal_windows(8))[0]
     assert np.abs(s0 - s1).max() < 1e-10 * np.abs(s0).max()
+
+
+def test_filter_apply_dense(oracle_lib):
+    """B F = sum_i v_i g(lambda_i) <v_i, F> with g(lambda) = sum_k c_k T_k(2 lambda - 1), from numpy's eigh
+    of the dense operator, per component."""
+    L = (2, 2, 2, 4)
+    U = inputs.random_links(L, eps=0.8, seed=45)
+    F = inputs.gaussian_fields(L, 1, seed=46)[0]
+    M = H.dense_operator(lambda X: oracle_lib.lap(L, U, X), L)
+    lam, vec = np.linalg.eigh(M)
+    coef = oracle_lib.window_coeffs([0.1, 0.35], 30)[0]
+    Y = oracle_lib.cheb_filter_apply(L, U, F, coef)
+    g = npcheb.chebval(2 * lam - 1, coef)
+    for c in range(4):
+        ref = vec @ (g * (vec.T @ F[:, c, :].ravel()))
+        assert np.abs(Y[:, c, :].ravel() - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_filter_apply_free_plane_wave_and_partition(oracle_lib):
+    """U = 1: a plane wave is an eigenvector, B X = g(lambda_k) X; and windows that partition [0, 1]
+    sum to the identity (their coefficients add up to delta_k0)."""
+    L = (4, 4, 6, 4)
+    U = inputs.unit_links(L)
+    X = H.plane_wave(L, (1, 2, 3, 0), 2, 5, 0.3)
+    lam = H.free_eigenvalue(L, (1, 2, 3, 0))
+    N = 60
+    edges = np.linspace(0.0, 1.0, 9)
+    C = oracle_lib.window_coeffs(edges, N)
+    total = np.zeros_like(X)
+    for w in range(8):
+        Y = oracle_lib.cheb_filter_apply(L, U, X, C[w])
+        assert np.abs(Y - npcheb.chebval(2 * lam - 1, C[w]) * X).max() < 1e-12
+        total += Y
+    assert np.abs(total - X).max() < 1e-12
