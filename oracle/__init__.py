@@ -386,7 +386,12 @@ def kinetic(L, U, P, mass, tol=1e-13):
 
 def heatbath(L, U, xi, mass, tol=1e-13):
     """Momentum refresh P = M^{1/2} xi, taken as m(A) R(A) xi with m(A) = (1-kappa) + kappa A
-    (R ~ m^{-1/2}, so m R ~ m^{1/2} = M^{1/2} to the accuracy of the rational fit)."""
+    (R ~ m^{-1/2}, so m R ~ m^{1/2} = M^{1/2} to the accuracy of the rational fit).  A general rational
+    mass (kappa = 0 with poles, e.g. fitted to a spectrum) has P = R(A)^{-1} xi exactly, here by CG on
+    the symmetric positive operator R(A), each application one set of shifted solves."""
+    if mass.get("kappa", 0.0) == 0.0 and len(mass["sigma"]) > 0:
+        P, _, _ = cg(lambda v: rational_apply(L, U, v, mass, 1e-2 * tol)[0], xi, tol=tol)
+        return P
     y, _ = rational_apply(L, U, xi, mass, tol)
     k = mass.get("kappa", 0.0)
     return (1.0 - k) * y + k * lap(L, U, y)

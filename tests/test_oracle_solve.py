@@ -99,3 +99,62 @@ def test_u1_frequency(oracle_lib, n, e):
     w1 = (beta / 6.0) * khat2 / (0.001 + 0.999 * khat2 / 16.0)
     assert abs(w1 - 16.0) < 0.05 * 16.0
     assert np.abs(acc1[:, :, 2] + w1 * b).max() < 1e-5 * w1 * np.abs(b).max()
+
+
+def test_spectrum_fit_recovers_exact_rational():
+    """A spectrum generated from R* = c* + sum alpha*_j/(lam + sigma_j) on the fit's own pole grid
+    (alpha* >= 0) is fitted exactly: M = R*^{-2} up to the normalisation M = 1 at the largest power."""
+    sigma = np.geomspace(1e-3, 10.0, 8)
+    rng = np.random.default_rng(11)
+    alpha = rng.uniform(0.0, 0.05, 8) * (rng.uniform(size=8) > 0.3)
+    Rstar = {"c": 0.3, "alpha": alpha, "sigma": sigma}
+    lam = (np.arange(64) + 0.5) / 64
+    spec = 5.0 * fit.evaluate(Rstar, lam) ** -2
+    m = fit.spectrum_mass_term(lam, spec, 8)
+    g = (spec / spec.max()) ** -0.5
+    assert np.abs(fit.evaluate(m, lam) / g - 1).max() < 1e-10
+    assert m["err"] < 1e-10 and m["kappa"] == 0.0 and m["c"] >= 0 and np.all(m["alpha"] >= 0)
+
+
+def test_spectrum_fit_linear_power():
+    """The near-linear power of Sec. 2 (s = 0.1 + lam): 12 poles fit M = s / max s to better than 1e-3,
+    and the fitted M increases with lam."""
+    lam = (np.arange(64) + 0.5) / 64
+    m = fit.spectrum_mass_term(lam, 0.1 + lam, 12)
+    assert m["err"] < 1e-3
+    M = fit.evaluate(m, np.linspace(0, 1, 201)) ** -2
+    assert np.all(np.diff(M) > 0)
+
+
+@pytest.mark.parametrize("c", [0.7, 0.0])
+def test_inverse_partial_fraction(c):
+    """(p0 + p1 lam + sum beta_j/(lam + zeta_j)) R(lam) = 1 on [0, 1] and beyond, with and without c."""
+    mass = {"c": c, "alpha": np.array([0.02, 0.3, 0.0, 1.5, 0.7]), "sigma": np.array([0.01, 0.2, 0.5, 1.3, 4.0])}
+    inv = fit.inverse_partial_fraction(mass)
+    lam = np.linspace(0.0, 3.0, 301)
+    r = inv["p0"] + inv["p1"] * lam + sum(b / (lam + z) for b, z in zip(inv["beta"], inv["zeta"]))
+    assert np.abs(r * fit.evaluate(mass, lam) - 1).max() < 1e-11
+    assert np.all(inv["zeta"] > 0)
+
+
+def test_general_heatbath_plane_wave(oracle_lib):
+    """U = 1: a plane wave of eigenvalue lam_k goes to X / R(lam_k) under the heatbath of a general
+    rational mass (kappa = 0)."""
+    L = (4, 4, 4, 4)
+    U = inputs.unit_links(L)
+    X = H.plane_wave(L, (1, 0, 2, 1), 3, 4, 0.1)
+    lam = H.free_eigenvalue(L, (1, 0, 2, 1))
+    mass = {"c": 0.4, "alpha": np.array([0.05, 0.2, 0.6]), "sigma": np.array([0.02, 0.3, 2.0]), "kappa": 0.0}
+    P = oracle_lib.heatbath(L, U, X, mass, tol=1e-13)
+    assert np.abs(P - X / fit.evaluate(mass, lam)).max() < 1e-11
+
+
+def test_general_heatbath_kinetic_identity(oracle_lib):
+    """T(P) = 1/2 |R P|^2 = 1/2 |xi|^2 for P = R^{-1} xi on random links."""
+    L = (2, 2, 2, 4)
+    U = inputs.random_links(L, eps=0.6, seed=12)
+    xi = inputs.gaussian_fields(L, 1, seed=13)[0]
+    mass = {"c": 0.4, "alpha": np.array([0.05, 0.2, 0.6]), "sigma": np.array([0.02, 0.3, 2.0]), "kappa": 0.0}
+    P = oracle_lib.heatbath(L, U, xi, mass, tol=1e-13)
+    T, _, _ = oracle_lib.kinetic(L, U, P, mass, tol=1e-14)
+    assert abs(T - 0.5 * np.sum(xi * xi)) < 1e-11 * T
