@@ -32,6 +32,8 @@ import subprocess
 
 import numpy as np
 
+from . import fit
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _lib = None
@@ -408,7 +410,39 @@ def _maxabs(a):
     return float(np.max(np.abs(a))) if a.size else 0.0
 
 
-def leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol=1e-13, fp_tol=1e-13, fp_maxit=100, FG=None):
+# --------------------------------------------------------------------------
+# Sec. 3: the log|M| term realised by an auxiliary field.  Integrating the momenta out of
+# exp(-1/2 P M^{-1} P) leaves det M^{1/2}; an auxiliary field phi with action S_aux = 1/2 <phi, M phi>
+# contributes det M^{-1/2}, so the links are distributed as exp(-S).  With M = R^{-2},
+# S_aux = 1/2 |Q phi|^2 with Q = 1/R (partial fraction p0 + sum_j beta_j/(A + zeta_j), c > 0), which
+# has the form of the kinetic energy with the mass term Q: its force is the kinetic force of phi
+# under Q.  phi is drawn once per trajectory, phi = M^{-1/2} eta = R(A) eta, and held fixed in the MD.
+# --------------------------------------------------------------------------
+
+def aux_mass(mass):
+    """The inverse mass term Q = 1/R as a partial fraction {c: p0, alpha: beta, sigma: zeta}."""
+    inv = fit.inverse_partial_fraction(mass)
+    if inv["p1"] != 0.0:
+        raise ValueError("the auxiliary field needs c > 0 (1/R without a linear term)")
+    return {"c": inv["p0"], "alpha": inv["beta"], "sigma": inv["zeta"], "kappa": 0.0}
+
+
+def aux_action(L, U, phi, mass, tol=1e-13):
+    """S_aux = 1/2 <phi, M phi> = 1/2 |Q phi|^2."""
+    T, _, _ = kinetic(L, U, phi, aux_mass(mass), tol)
+    return T
+
+
+def potential_force(L, U, beta, c1, mass=None, phi=None, tol=1e-13):
+    """F_G(U), plus the auxiliary-field force -d S_aux/dw when phi is given."""
+    F = gauge_force(L, U, beta, c1)
+    if phi is not None:
+        _, FA, _ = kinetic(L, U, phi, aux_mass(mass), tol)
+        F = F + FA
+    return F
+
+
+def leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol=1e-13, fp_tol=1e-13, fp_maxit=100, FG=None, phi=None):
     """One generalised-leapfrog step (Sec. 3; Girolami & Calderhead) on SU(3):
       (1) P' = P + eps/2 F(U, P')                      [fixed point]
       (2) U' = exp(i eps/2 V(U',P')) exp(i eps/2 V(U,P')) U   [fixed point]
@@ -420,10 +454,11 @@ def leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol=1e-13, fp_tol=1e-13, fp_
     The Lie-Poisson term of the group flow is not included (it changes neither H nor the
     phase-space volume of the continuous flow); exact volume preservation of this discrete
     group step: parity unpinned.
-    FG (optional) is F_G(U) if the caller has it.
+    FG (optional) is F_G(U) if the caller has it.  With an auxiliary field phi, F_G stands for the whole
+    potential force F_G + F_aux (both depend on U only).
     Returns (U'', P'', next initial guess, iteration counts, F_G(U''))."""
     if FG is None:
-        FG = gauge_force(L, U, beta, c1)
+        FG = potential_force(L, U, beta, c1, mass, phi, tol)
     Q = Q0
     for i1 in range(1, fp_maxit + 1):
         _, FK, V0 = kinetic(L, U, Q, mass, tol)
@@ -446,37 +481,44 @@ def leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol=1e-13, fp_tol=1e-13, fp_
             break
     else:
         raise RuntimeError("oracle: link fixed point did not converge")
-    FG1 = gauge_force(L, W, beta, c1)
+    FG1 = potential_force(L, W, beta, c1, mass, phi, tol)
     P2 = Ph + 0.5 * eps * (FG1 + FK1)
     Qnext = P2 + 0.5 * eps * (FG1 + FK1)
     return W, P2, Qnext, (i1, i2), FG1
 
 
-def md_trajectory(L, U, P, tau, nsteps, beta, c1, mass, tol=1e-13, fp_tol=1e-13, fp_maxit=100):
+def md_trajectory(L, U, P, tau, nsteps, beta, c1, mass, tol=1e-13, fp_tol=1e-13, fp_maxit=100, phi=None):
     """nsteps generalised-leapfrog steps of size tau/nsteps; the first momentum
-    fixed point starts from P + eps/2 F_G(U)."""
+    fixed point starts from P + eps/2 F_G(U) (F_G + F_aux with an auxiliary field phi)."""
     eps = tau / nsteps
-    FG = gauge_force(L, U, beta, c1)
+    FG = potential_force(L, U, beta, c1, mass, phi, tol)
     Q0 = P + 0.5 * eps * FG
     iters = []
     for _ in range(nsteps):
-        U, P, Q0, it, FG = leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol, fp_tol, fp_maxit, FG)
+        U, P, Q0, it, FG = leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol, fp_tol, fp_maxit, FG, phi)
         iters.append(it)
     return U, P, iters
 
 
 def trajectory(L, U, xi, u, tau, nsteps, beta, c1, mass, tol_md=1e-13, tol_h=1e-13,
-               fp_tol=1e-13, fp_maxit=100, metropolis=True):
-    """One RMHMC trajectory: heatbath P = M^{1/2} xi, H0, MD, H1, accept if u <= exp(-dH)."""
+               fp_tol=1e-13, fp_maxit=100, metropolis=True, eta=None):
+    """One RMHMC trajectory: heatbath P = M^{1/2} xi, H0, MD, H1, accept if u <= exp(-dH).
+    With eta (a Gaussian field), the log|M| term is included through the auxiliary field
+    phi = R(A) eta, held fixed in the MD, and H = T + S + S_aux."""
+    phi = rational_apply(L, U, eta, mass, tol_h)[0] if eta is not None else None
     P0 = heatbath(L, U, xi, mass, tol_h)
     H0, T0, S0, _ = hamiltonian(L, U, P0, beta, c1, mass, tol_h)
-    U1, P1, iters = md_trajectory(L, U, P0, tau, nsteps, beta, c1, mass, tol_md, fp_tol, fp_maxit)
+    A0 = aux_action(L, U, phi, mass, tol_h) if phi is not None else 0.0
+    U1, P1, iters = md_trajectory(L, U, P0, tau, nsteps, beta, c1, mass, tol_md, fp_tol, fp_maxit, phi)
     H1, T1, S1, plaq1 = hamiltonian(L, U1, P1, beta, c1, mass, tol_h)
+    A1 = aux_action(L, U1, phi, mass, tol_h) if phi is not None else 0.0
+    H0 += A0
+    H1 += A1
     dH = H1 - H0
     accept = (not metropolis) or (u <= math.exp(-dH) if dH > 0 else True)
     Uout = U1 if accept else U
     return {"U": Uout, "U1": U1, "P0": P0, "P1": P1, "H0": H0, "H1": H1, "dH": dH,
-            "T0": T0, "S0": S0, "T1": T1, "S1": S1, "accepted": bool(accept),
+            "T0": T0, "S0": S0, "T1": T1, "S1": S1, "A0": A0, "A1": A1, "accepted": bool(accept),
             "plaq": action(L, Uout, beta, c1)[1], "iters": iters}
 
 

@@ -124,3 +124,53 @@ def test_plain_hmc_exp_minus_dH(oracle_lib):
         vals.append(math.exp(-r["dH"]))
     vals = np.array(vals)
     assert abs(vals.mean() - 1.0) < 4 * vals.std() / math.sqrt(len(vals)) + 1e-3
+
+
+def test_aux_action_is_half_eta_squared(oracle_lib):
+    """phi = R(A) eta gives S_aux = 1/2 <phi, M phi> = 1/2 |eta|^2 (M = R^{-2})."""
+    L = L2
+    U = inputs.random_links(L, eps=0.5, seed=71)
+    eta = inputs.gaussian_fields(L, 1, seed=72)[0]
+    m = fit.mass_term(12, 0.9)
+    phi = oracle_lib.rational_apply(L, U, eta, m, 1e-14)[0]
+    S = oracle_lib.aux_action(L, U, phi, m, 1e-14)
+    assert abs(S - 0.5 * np.sum(eta * eta)) < 1e-11 * S
+
+
+def test_aux_force_finite_difference(oracle_lib):
+    """The auxiliary-field force is -dS_aux/dw (central differences along random single-link directions)."""
+    L = L2
+    U = inputs.random_links(L, eps=0.5, seed=73)
+    phi = inputs.gaussian_fields(L, 1, seed=74)[0]
+    m = fit.mass_term(8, 0.9)
+    F = oracle_lib.potential_force(L, U, 6.0, 0.0, m, phi, 1e-14) - oracle_lib.gauge_force(L, U, 6.0, 0.0)
+    rng = np.random.default_rng(75)
+    h = 1e-5
+    for _ in range(6):
+        y, nu = int(rng.integers(0, 16)), int(rng.integers(0, 4))
+        d = rng.standard_normal(8)
+        vals = []
+        for sgn in (+1, -1):
+            Up = U.copy()
+            Up[y, nu] = H.mm(oracle_lib.exp_i(sgn * h * d), U[y, nu])
+            vals.append(oracle_lib.aux_action(L, Up, phi, m, 1e-14))
+        fd = -(vals[0] - vals[1]) / (2 * h)
+        an = float(F[y, nu] @ d)
+        assert abs(fd - an) < 1e-6 * max(1.0, abs(an))
+
+
+def test_aux_energy_error_scales_as_step_squared(oracle_lib):
+    """With the auxiliary field in H and its force in the MD, dH still falls as the step size squared."""
+    L = L2
+    U = inputs.random_links(L, eps=0.3, seed=76)
+    P = inputs.gaussian_fields(L, 1, seed=77)[0]
+    eta = inputs.gaussian_fields(L, 1, seed=78)[0]
+    m = fit.mass_term(8, 0.9)
+    phi = oracle_lib.rational_apply(L, U, eta, m, 1e-14)[0]
+    H = lambda U_, P_: (oracle_lib.hamiltonian(L, U_, P_, 6.0, 0.0, m)[0] + oracle_lib.aux_action(L, U_, phi, m))
+    dH = []
+    for n in (5, 10):
+        H0 = H(U, P)
+        U1, P1, _ = oracle_lib.md_trajectory(L, U, P, 0.5, n, 6.0, 0.0, m, phi=phi)
+        dH.append(H(U1, P1) - H0)
+    assert 3.0 < dH[0] / dH[1] < 5.0, dH
