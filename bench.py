@@ -14,6 +14,7 @@ Prints one JSON line (rank 0).  --impl reference times the float64 CPU oracle in
 """
 import argparse
 import json
+import re
 import math
 import os
 import subprocess
@@ -34,6 +35,10 @@ NSTEPS = 20
 CHEB_DEGREE = 200
 CHEB_WINDOWS = 64
 CHEB_NOISE = 16
+# DRAM bytes (read + write) of one k_cg_A<float,18> launch at 32^4 with k > 0, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_cg_A_fp32_32x32x32x32.md), per tuned launch shape
+# (components per lane, threads per block); a shape without a capture reports null
+CG_TRAFFIC_32 = {(2, 256): 846.0e6}
 # algorithmic bytes per site of the conjugate-gradient stencil k_cg_A<float,18> (float32, 18-real links):
 # read r_k (128 B) and q_{k-1} (128 B), write q_k (128 B), four links of 72 B
 CG_BYTES_PER_SITE = 3 * 128 + 4 * 72
@@ -109,9 +114,9 @@ def replica_seeds(rank):
 
 
 def oracle_sample(seconds_cap=30.0):
-    """Time the float64 CPU oracle on a bounded sample of the workload: one kinetic-force evaluation
-    (two 12-shift rational solves by per-shift CG, plus the link gradient) and one Laplacian
-    application at 8^4 with the workload's mass term and link recipe."""
+    """Time the float64 CPU oracle on a bounded sample of the workload (about 10 s): kinetic-force
+    evaluations (two 12-shift rational solves by per-shift CG, plus the link gradient) and Laplacian
+    applications at 8^4 with the workload's mass term and link recipe."""
     import numpy as np
 
     import oracle
@@ -122,9 +127,13 @@ def oracle_sample(seconds_cap=30.0):
     U = inputs.random_links(L, eps=0.3, seed=0)
     P = inputs.gaussian_fields(L, 1, seed=1)[0]
     m = fit.mass_term(NPOLE, KAPPA)
+    # repeat the kinetic evaluation until about 8 s of CPU work (at least twice) and average
     t0 = time.perf_counter()
-    oracle.kinetic(L, U, P, m, tol=1e-6)
-    t_kin = time.perf_counter() - t0
+    nkin = 0
+    while nkin < 2 or time.perf_counter() - t0 < 8.0:
+        oracle.kinetic(L, U, P, m, tol=1e-6)
+        nkin += 1
+    t_kin = (time.perf_counter() - t0) / nkin
     t0 = time.perf_counter()
     nlap = 0
     while time.perf_counter() - t0 < 2.0:
@@ -142,12 +151,19 @@ def oracle_traj_seconds(s, md_solves):
     return s["scale"] * ((md_solves + 3) * s["t_kin_8"] + 18 * CHEB_DEGREE // 2 * s["t_lap_8"])
 
 
+def workload_config(nsteps, world):
+    return {"workload": "32^4 full RMHMC (Wilson beta 6.0, 12-pole mass kappa 0.9, tau 1, %d steps, "
+                        "mixed precision) + gauge-force spectrum (degree 200, 64 windows, 16 noise)" % nsteps,
+            "lattice": "x".join(str(d) for d in DIMS), "l2": "working set > L2, no flush",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
     s0 = time.perf_counter()
     vals = []
-    md_solves = 150   # kinetic evaluations of one 20-step trajectory (the mixed GPU run measures ~150)
+    md_solves = 161   # kinetic evaluations of one 20-step trajectory (the GPU runs measure 81 + 80)
     for i in range(args.warmup + args.steps):
         s = oracle_sample()
         if i >= args.warmup:
@@ -159,8 +175,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "traj/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "32^4 full RMHMC (beta 6.0, 12-pole mass kappa 0.9, tau 1, 20 steps) + "
-                                   "gauge-force spectrum (degree 200, 64 windows)", "lattice": "32^4"},
+            "config": workload_config(args.nsteps, world),
             "cpu_baseline": {"value": value, "unit": "traj/s", "cores": s["cores"], "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "traj/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -328,9 +343,12 @@ def main():
     cg_avg_ms = cnt["cg_ms"] / max(cnt["cg_count"], 1)
     achieved = cg_bytes / (cg_avg_ms * 1e-3) / 1e9 if cnt["cg_count"] else None
     alu_fma = 5000.0 * V   # per site: 8 hops x 4 components x 144 FMA + the fused axpy and epilogue
+    m = re.search(r"cg fp32 -> nmu (\d+) block (\d+)", rm.tuning(lat))
+    shape = (int(m.group(1)), int(m.group(2))) if m else None
+    traffic = CG_TRAFFIC_32.get(shape) if DIMS == (32, 32, 32, 32) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None, "peak_kind": peak_kind,
-                "kernel": "k_cg_A<float,18> (CG stencil)", "launches": cnt["cg_count"],
+                "frac": achieved / peak if achieved else None, "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "k_cg_A<float,18> (CG stencil)", "shape": shape, "launches": cnt["cg_count"],
                 "avg_launch_ms": cg_avg_ms, "alu_tfma_s": alu_fma / (cg_avg_ms * 1e-3) / 1e12 if cnt["cg_count"] else None,
                 "alu_peak_tfma_s": 37.4}
 
@@ -373,11 +391,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "traj/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "32^4 full RMHMC (Wilson beta 6.0, 12-pole mass kappa 0.9, tau 1, %d steps, "
-                                   "mixed precision) + gauge-force spectrum (degree 200, 64 windows, 16 noise)"
-                                   % args.nsteps,
-                       "lattice": "x".join(str(d) for d in DIMS), "l2": "working set > L2, no flush",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": workload_config(args.nsteps, world),
             "thermalisation_plaq": therm[-3:] if therm else None,
             "autotune": rm.tuning(lat),
             "roofline": roofline, "clocks": clk, "gpu_launches": cnt["launches"],

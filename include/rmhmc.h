@@ -105,10 +105,13 @@ typedef struct {
     uint64_t seed;      /* Philox key for the heatbath noise and the Metropolis uniform */
     uint32_t traj_index;/* Philox stream: trajectory number */
     int metropolis;     /* 1: accept/reject with probability min(1, exp(-dH)); 0: always accept */
+    int logdet;         /* 1: the log|M| term of Eq. (5) through an auxiliary field phi = R(A) eta (eta from
+                           Philox(seed, traj_index, tag 3)), held fixed in the MD, with action
+                           1/2 <phi, M phi> = 1/2 |R(A)^{-1} phi|^2 in H and its force in the MD (needs c > 0) */
 } rmhmc_params;
 
 typedef struct {
-    double dH, H0, H1;  /* Hamiltonian (Eq. 5 without log|M|) before and after the MD */
+    double dH, H0, H1;  /* Hamiltonian (Eq. 5; the log|M| term through the auxiliary field when logdet) */
     double T0, S0, T1, S1;
     double plaq;        /* average plaquette ReTr/3 of the output configuration */
     double u;           /* the uniform used by the Metropolis test */
@@ -118,6 +121,7 @@ typedef struct {
     int fp_iters_p;     /* momentum fixed-point iterations, summed over steps */
     int fp_iters_u;     /* link fixed-point iterations, summed over steps */
     double max_fp_change;
+    double A0, A1;      /* auxiliary-field action before and after the MD (0 without logdet); H includes it */
 } rmhmc_result;
 
 /* ---------------------------------------------------------------------------------------------- */
@@ -219,7 +223,10 @@ int rat_mass_solve(rmhmc_ctx* ctx, const double* U, const double* b, int nshift,
                    int prec, double* y, double* xs, int* iters, double* resid, cudaStream_t stream);
 
 /* Momentum heatbath (Sec. 3): P = m(A) R(A) xi with m(A) = (1-kappa) + kappa A, so that P has
- * covariance M = R^{-2} up to the fit error.  xi, P: device float64 [V][4][8]. */
+ * covariance M = R^{-2} up to the fit error.  A general rational mass (kappa = 0 with poles, e.g. from
+ * rmhmc_mass_fit_spectrum; c >= 0, alpha_j >= 0) gets P = R(A)^{-1} xi exactly, from the partial fraction
+ * 1/R = p0 + p1 lam + sum_j beta_j/(lam + zeta_j) (zeros of R found on the host).  xi, P: device float64
+ * [V][4][8]. */
 int rmhmc_heatbath(rmhmc_ctx* ctx, const double* U, const double* xi, const rmhmc_mass* mass,
                    double tol, int prec, double* P, cudaStream_t stream);
 
@@ -228,6 +235,18 @@ int rmhmc_heatbath(rmhmc_ctx* ctx, const double* U, const double* xi, const rmhm
  * (nullable) receives max |R m^{1/2} - 1| on a 4096-point grid. */
 int rmhmc_mass_fit(int npole, double kappa, double* c, double* alpha, double* sigma,
                    double* max_rel_err);
+
+/* Mass term fitted to a measured force power spectrum per mode (Sec. 4; e.g. the spec output of
+ * cheb_filter_spectrum at the window centres lam): M(lam) proportional to s(lam), normalised to 1 at the largest
+ * power, so that every Laplacian mode moves at the same MD rate.  R = M^{-1/2} = c + sum_j alpha_j/(lam + sigma_j)
+ * with the npole poles fixed on a geometric grid in [sigma_min, sigma_max] and c, alpha_j >= 0 minimising
+ * sum_w (R(lam_w) (s_w / max s)^{1/2} - 1)^2 (non-negative least squares), so M = R^{-2} is positive and
+ * increasing.  Host outputs c, alpha[npole], sigma[npole]; max_rel_err (nullable) receives the largest
+ * relative error of R at the lam_w.  Use the result with kappa = 0 (a general rational mass: the heatbath is
+ * then P = R(A)^{-1} xi).  RMHMC_EINVAL for nwin < 1, npole outside [0, 24], lam outside [0, 1], a
+ * non-positive power or a bad pole range. */
+int rmhmc_mass_fit_spectrum(int nwin, const double* lam, const double* spec, int npole, double sigma_min,
+                            double sigma_max, double* c, double* alpha, double* sigma, double* max_rel_err);
 
 /* Allocation-free gauge action: the paper has no counterpart; this is a service for callers that cannot
  * allocate device memory -- code that is capturing a CUDA graph (cudaMalloc is not capturable) or an
@@ -282,7 +301,8 @@ int rmhmc_hamiltonian(rmhmc_ctx* ctx, const double* U, const double* P, const rm
 
 /* Molecular dynamics only: p->nsteps generalised-leapfrog steps of size p->tau / p->nsteps on
  * (U, P) in place (device canonical links, device float64 momenta), with the implicit fixed points
- * of Sec. 3.  r (nullable) receives the iteration counts. */
+ * of Sec. 3.  r (nullable) receives the iteration counts.  p->logdet is not used here (the auxiliary
+ * field belongs to a trajectory: rmhmc_trajectory). */
 int rmhmc_md(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, rmhmc_result* r,
              cudaStream_t stream);
 
@@ -292,6 +312,31 @@ int rmhmc_md(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, rmhmc_
  * (device, nullable) receives the final momenta of the MD. */
 int rmhmc_trajectory(rmhmc_ctx* ctx, double* U, const double* xi, const rmhmc_params* p,
                      rmhmc_result* r, double* P_out, cudaStream_t stream);
+
+/* Chebyshev coefficients of spectral windows, Sec. 2 Eq. (4): C[w][k], w < nwin, k <= degree, of the indicator of
+ * [edges[w], edges[w+1]] (eigenvalues of A in [0, 1]; variable x = 2 lambda - 1), times Jackson's damping when
+ * kernel == RMHMC_KERNEL_JACKSON.  Host only.  C: nwin * (degree + 1) doubles (caller's).  RMHMC_EINVAL for
+ * edges that do not increase within [0, 1], degree outside [0, 20000] or a bad kernel. */
+int cheb_window_coeffs(int nwin, const double* edges, int degree, int kernel, double* C);
+
+/* A band filter applied as a vector (the band-filtered momenta of Sec. 4): Y_f = sum_{k=0}^{degree} coef[k]
+ * T_k(2A - 1) F_f for nfield fields, F and Y device float64 [nfield][V][4][8] (16-byte aligned, distinct),
+ * coef host (degree + 1 doubles, e.g. a row of cheb_window_coeffs).  degree stencil applications by the
+ * three-term recurrence; prec RMHMC_FP64, or RMHMC_MIXED (float32 recurrence, float64 accumulation).
+ * U as in lap_apply (NULL: the context's links).  RMHMC_EINVAL for bad sizes, a bad prec or misalignment. */
+int cheb_filter_apply(rmhmc_ctx* ctx, const double* U, const double* F, int nfield, int degree, const double* coef,
+                      int prec, double* Y, cudaStream_t stream);
+
+/* Wilson gradient flow, the flowed-energy observable of Sec. 4 (the paper takes its definition from
+ * Luscher, JHEP 08 (2010) 071): nsteps steps of size eps of Luscher's third-order Runge-Kutta scheme for
+ * dV/dt = -g0^2 (dS_W) V, in place on U (device, canonical complex128 [V][4][3][3]).  The flow does not
+ * depend on beta (g0^2 F = 6 F at beta = 1).  E (host, nullable, nsteps + 1 doubles) receives the plaquette
+ * energy density E = (1/V) sum_x 2 sum_{mu<nu} Re Tr(1 - P_mu,nu(x)) = 36 (1 - <Re Tr P / 3>) at
+ * t = 0, eps, ..., nsteps eps; t^2 E(t) is the usual scale-setting combination.  prec RMHMC_FP64 (all
+ * float64) or RMHMC_MIXED (float32 force, float64 links and updates).  The context's link copies hold the
+ * flowed links afterwards.  Synchronous.  RMHMC_EINVAL for a NULL or misaligned U, nsteps < 0, a
+ * non-finite eps or a bad prec. */
+int wilson_flow(rmhmc_ctx* ctx, double* U, double eps, int nsteps, int prec, double* E, cudaStream_t stream);
 
 #if defined(__GNUC__)
 #pragma GCC visibility pop

@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
                 ("nsteps", ctypes.c_int), ("tol_md", ctypes.c_double), ("tol_h", ctypes.c_double),
                 ("fp_tol", ctypes.c_double), ("fp_maxit", ctypes.c_int), ("maxiter", ctypes.c_int),
                 ("prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("traj_index", ctypes.c_uint32),
-                ("metropolis", ctypes.c_int)]
+                ("metropolis", ctypes.c_int), ("logdet", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -50,7 +50,8 @@ class Result(ctypes.Structure):
                 ("T0", ctypes.c_double), ("S0", ctypes.c_double), ("T1", ctypes.c_double), ("S1", ctypes.c_double),
                 ("plaq", ctypes.c_double), ("u", ctypes.c_double), ("accepted", ctypes.c_int),
                 ("md_solves", ctypes.c_int), ("md_iters", ctypes.c_longlong), ("fp_iters_p", ctypes.c_int),
-                ("fp_iters_u", ctypes.c_int), ("max_fp_change", ctypes.c_double)]
+                ("fp_iters_u", ctypes.c_int), ("max_fp_change", ctypes.c_double), ("A0", ctypes.c_double),
+                ("A1", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -93,6 +94,10 @@ def lib():
         "rmhmc_set_profiling": ([P, I], I),
         "rmhmc_tuning": ([P, ctypes.c_char_p, I], I),
         "rmhmc_set_graphs": ([P, I], I),
+        "wilson_flow": ([P, P, D, I, I, DP, P], I),
+        "cheb_window_coeffs": ([I, DP, I, I, DP], I),
+        "rmhmc_mass_fit_spectrum": ([I, DP, DP, I, D, D, DP, DP, DP, DP], I),
+        "cheb_filter_apply": ([P, P, P, I, I, DP, I, P, P], I),
         "rmhmc_get_counters": ([P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(ctypes.c_longlong), DP, I], I),
     }
@@ -338,12 +343,89 @@ def link_update(ctx, U, V, eps, reunit=True, out=None, stream=None):
     return out
 
 
+def mass_fit_spectrum(lam, spec, npole=12, sigma_min=1e-3, sigma_max=10.0):
+    """Mass term fitted to a measured power spectrum per mode (M proportional to the power, M = 1 at its
+    maximum); returns a general rational mass dict (kappa = 0)."""
+    import numpy as np
+    la, lp = _dbl(lam)
+    sa, sp = _dbl(spec)
+    c = ctypes.c_double()
+    err = ctypes.c_double()
+    alpha = np.zeros(npole)
+    sigma = np.zeros(npole)
+    P = ctypes.POINTER(ctypes.c_double)
+    code = lib().rmhmc_mass_fit_spectrum(len(la), lp, sp, int(npole), float(sigma_min), float(sigma_max),
+                                         ctypes.byref(c), alpha.ctypes.data_as(P), sigma.ctypes.data_as(P),
+                                         ctypes.byref(err))
+    if code != 0:
+        raise RmhmcError(code, "rmhmc_mass_fit_spectrum: bad arguments")
+    return {"c": c.value, "alpha": alpha, "sigma": sigma, "kappa": 0.0, "err": err.value}
+
+
+def window_coeffs(edges, degree, kernel=KERNEL_JACKSON):
+    """C[w, k] of the windows [edges[w], edges[w+1]] (numpy [nwin, degree+1]), computed by the library."""
+    import numpy as np
+    e, ep = _dbl(edges)
+    C = np.zeros((len(e) - 1, int(degree) + 1))
+    code = lib().cheb_window_coeffs(len(e) - 1, ep, int(degree), int(kernel),
+                                    C.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if code != 0:
+        raise RmhmcError(code, "cheb_window_coeffs: bad windows, degree or kernel")
+    return C
+
+
+def cheb_filter_apply(ctx, U, F, coef, prec=FP64, out=None, stream=None):
+    """Y = sum_k coef[k] T_k(2A - 1) F for F of shape [V,4,8] or [nfield,V,4,8] (float64, device)."""
+    import numpy as np
+    import torch
+    c, cp = _dbl(coef)
+    Fc = F.contiguous()
+    nf = 1 if Fc.dim() == 3 else Fc.shape[0]
+    if out is None:
+        out = torch.empty_like(Fc)
+    ctx.check(lib().cheb_filter_apply(ctx.h, _links(U), _ptr(Fc), nf, len(c) - 1, cp, int(prec), _ptr(out),
+                                      _stream(stream)))
+    return out
+
+
+def band_injection(ctx, U, xi, mass, window, degree=200, md_eps=1e-4, beta=6.0, c1=0.0, flow_t=8.0,
+                   flow_eps=0.01, prec=FP64, tol=1e-12):
+    """The momentum-injection experiment of Sec. 4 (Fig. 2): heatbath momenta P = M^{1/2} xi filtered to the
+    window [a, b] of Laplacian eigenvalues, one leapfrog step of md_eps from (U, P_w), and the change of the
+    Wilson-flowed energy at flow time flow_t.  Every step runs in the library's kernels; U is not modified.
+    Returns (E_t(U'), E_t(U), P_w)."""
+    import numpy as np
+    C = window_coeffs(np.array(window, dtype=np.float64), degree)[0]
+    P = heatbath(ctx, U, xi, mass, tol=tol, prec=prec)
+    Pw = cheb_filter_apply(ctx, U, P, C, prec=prec)
+    U1 = U.clone()
+    Pm = Pw.clone()
+    md(ctx, U1, Pm, make_params(beta=beta, c1=c1, mass=mass, tau=md_eps, nsteps=1, tol_md=tol, tol_h=tol,
+                                fp_tol=tol, prec=prec, metropolis=False))
+    n = int(round(flow_t / flow_eps))
+    U0 = U.clone()
+    E0 = wilson_flow(ctx, U0, flow_eps, n, prec=prec)[-1]
+    E1 = wilson_flow(ctx, U1, flow_eps, n, prec=prec)[-1]
+    return E1, E0, Pw
+
+
+def wilson_flow(ctx, U, eps, nsteps, prec=FP64, stream=None):
+    """Wilson gradient flow of U in place (nsteps Runge-Kutta steps of size eps); returns E(t) at
+    t = 0, eps, ..., nsteps*eps as a numpy array."""
+    import numpy as np
+    E = np.zeros(int(nsteps) + 1)
+    ctx.check(lib().wilson_flow(ctx.h, _links(U), float(eps), int(nsteps), int(prec),
+                                E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)))
+    return E
+
+
 def make_params(beta=6.0, c1=0.0, mass=None, tau=1.0, nsteps=20, tol_md=1e-10, tol_h=1e-11, fp_tol=1e-10,
-                fp_maxit=50, maxiter=2000, prec=FP64, seed=0, traj_index=0, metropolis=True):
+                fp_maxit=50, maxiter=2000, prec=FP64, seed=0, traj_index=0, metropolis=True, logdet=False):
     mass = mass if mass is not None else {"c": 1.0, "alpha": [], "sigma": [], "kappa": 0.0}
     ms = _mass_struct(mass)
     p = Params(float(beta), float(c1), ms, float(tau), int(nsteps), float(tol_md), float(tol_h),
-               float(fp_tol), int(fp_maxit), int(maxiter), int(prec), int(seed), int(traj_index), int(bool(metropolis)))
+               float(fp_tol), int(fp_maxit), int(maxiter), int(prec), int(seed), int(traj_index), int(bool(metropolis)),
+               int(bool(logdet)))
     p._keep = ms._keep   # the struct copy holds raw pointers into these arrays
     return p
 

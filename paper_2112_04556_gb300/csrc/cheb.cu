@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "krylov.cuh"
 #include "ops.cuh"
 #include "philox.cuh"
 
@@ -126,9 +127,66 @@ static int cheb_run(rmhmc_ctx* ctx, const double* fields64, int nr, int N, int p
     return RMHMC_OK;
 }
 
+// y (float64) += c x (x in the recurrence precision), grid-stride
+template <typename T>
+__global__ void k_accum64(const T* __restrict__ x, double c, double* __restrict__ y, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = fma(c, (double)x[i], y[i]);
+}
+
+// Y = sum_k coef[k] T_k(2A - 1) F by the forward recurrence, accumulating every term in float64
+template <typename T>
+static int filter_run(rmhmc_ctx* ctx, const double* F, int nf, int N, const double* coef, int prec, double* Y,
+                      cudaStream_t st) {
+    int status = RMHMC_OK;
+    const size_t fs = field_elems(ctx), n = fs * nf;
+    const bool f32 = sizeof(T) == 4;
+    T* buf = (T*)workspace(ctx, f32 ? "cf_v32" : "cf_v64", sizeof(T) * n * 3, &status);
+    if (!buf) return status;
+    T* v[3] = {buf, buf + n, buf + 2 * n};
+    if (f32) RM_TRY(to_float(ctx, F, (float*)v[0], n, st));
+    else RM_CHECK(ctx, cudaMemcpyAsync(v[0], F, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    const int grid = capped_grid(ctx, n, kBlock);
+    RM_CHECK(ctx, cudaMemsetAsync(Y, 0, sizeof(double) * n, st));
+    k_accum64<T><<<grid, kBlock, 0, st>>>(v[0], coef[0], Y, n); ++ctx->launches;
+    for (int k = 1; k <= N; k++) {
+        T* out = v[k % 3];
+        const T* in = v[(k - 1) % 3];
+        const T* w = k >= 2 ? v[(k - 2) % 3] : nullptr;
+        RM_TRY(launch_lap(ctx, prec, 18, in, out, nf, 0.0, k == 1 ? -0.125 : -0.25, w, -1.0, -1, st));
+        k_accum64<T><<<grid, kBlock, 0, st>>>(out, coef[k], Y, n); ++ctx->launches;
+    }
+    RM_LAUNCH_CHECK(ctx);
+    return RMHMC_OK;
+}
+
 }  // namespace rm
 
 using namespace rm;
+
+extern "C" int cheb_window_coeffs(int nwin, const double* edges, int degree, int kernel, double* C) {
+    if (nwin < 1 || !edges || !C || degree < 0 || degree > 20000) return RMHMC_EINVAL;
+    if (kernel != RMHMC_KERNEL_NONE && kernel != RMHMC_KERNEL_JACKSON) return RMHMC_EINVAL;
+    for (int w = 0; w < nwin; w++)
+        if (!(edges[w] < edges[w + 1]) || edges[w] < 0.0 || edges[w + 1] > 1.0) return RMHMC_EINVAL;
+    std::vector<double> c;
+    window_coefficients(edges, nwin, degree, kernel == RMHMC_KERNEL_JACKSON, c);
+    memcpy(C, c.data(), sizeof(double) * c.size());
+    return RMHMC_OK;
+}
+
+extern "C" int cheb_filter_apply(rmhmc_ctx* ctx, const double* U, const double* F, int nfield, int degree,
+                                 const double* coef, int prec, double* Y, cudaStream_t stream) {
+    if (!ctx) return RMHMC_EINVAL;
+    ctx->err.clear();
+    if (!F || !Y || !coef || nfield < 1) return set_err(ctx, RMHMC_EINVAL, "cheb_filter_apply: bad fields");
+    if (degree < 0 || degree > 20000) return set_err(ctx, RMHMC_EINVAL, "cheb_filter_apply: degree in [0, 20000]");
+    if (prec != RMHMC_FP64 && prec != RMHMC_MIXED) return set_err(ctx, RMHMC_EINVAL, "cheb_filter_apply: bad prec");
+    if ((uintptr_t)F % 16 || (uintptr_t)Y % 16) return set_err(ctx, RMHMC_EINVAL, "cheb_filter_apply: misaligned field");
+    RM_TRY(ensure_links(ctx, U, stream));
+    if (prec == RMHMC_FP64) return filter_run<double>(ctx, F, nfield, degree, coef, prec, Y, stream);
+    return filter_run<float>(ctx, F, nfield, degree, coef, prec, Y, stream);
+}
 
 extern "C" int cheb_filter_spectrum(rmhmc_ctx* ctx, const double* U, const double* F, int nF, const double* noise,
                                     int nnoise, uint64_t seed, int degree, int nwin, const double* edges, int kernel,

@@ -275,6 +275,8 @@ struct rmhmc_ctx {
     float4* u32a = nullptr;
     float2* u32b = nullptr;
     bool links_valid = false;
+    unsigned long long link_gen = 1;   // bumped whenever the internal link copies change
+    unsigned long long adj_gen = 0;    // link_gen the adjoint table was built for
     // reductions
     double* red_partials = nullptr;   // [kRedSlots][max_blocks * 2]
     unsigned* red_counters = nullptr; // [kRedSlots]

@@ -98,6 +98,7 @@ int import_links(rmhmc_ctx* ctx, const double* U, cudaStream_t st) {
     k_import_links<<<site_blocks(ctx), kBlock, 0, st>>>(U, ctx->u64, ctx->u32a, ctx->u32b, ctx->g.V); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     ctx->links_valid = true;
+    ctx->link_gen++;
     return RMHMC_OK;
 }
 

@@ -156,8 +156,9 @@ __global__ void __launch_bounds__(kBlock) k_link_update(const double* __restrict
                                                         double eps, int reunit, double* __restrict__ Uout,
                                                         const double* __restrict__ Wold, double* maxdiff,
                                                         double2* u64, float4* u32a, float2* u32b, int nsite) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int mu = blockIdx.y;
+    // one thread per link, links of a site adjacent: a warp reads 32 consecutive 144-byte link records
+    const int lk = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = lk >> 2, mu = lk & 3;
     double diff = 0.0;
     if (s < nsite) {
         const size_t l = (size_t)s * 4 + mu;
@@ -220,8 +221,8 @@ __global__ void __launch_bounds__(kBlock) k_link_update(const double* __restrict
 __global__ void __launch_bounds__(kBlock) k_link_iter32(const double* __restrict__ B, const double* __restrict__ V,
                                                         float eps, float* __restrict__ W32, int have_old,
                                                         double* maxdiff, float4* u32a, float2* u32b, int nsite) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int mu = blockIdx.y;
+    const int lk = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = lk >> 2, mu = lk & 3;
     float diff = 0.f;
     if (s < nsite) {
         const size_t l = (size_t)s * 4 + mu;
@@ -314,13 +315,16 @@ __global__ void k_gauss_field(double* __restrict__ out, int V, uint64_t seed, ui
 // ------------------------------------------------------------------------------------------------
 // host driver
 // ------------------------------------------------------------------------------------------------
-static int link_update_launch(rmhmc_ctx* ctx, const double* Uin, const double* V, double eps, bool reunit, double* Uout,
-                              const double* Wold, double* dmax, bool internal, cudaStream_t st) {
-    const dim3 grid(site_blocks(ctx), 4);
+int link_update_launch(rmhmc_ctx* ctx, const double* Uin, const double* V, double eps, bool reunit, double* Uout,
+                       const double* Wold, double* dmax, bool internal, cudaStream_t st) {
+    const int grid = lane_blocks(ctx);   // 4 V threads
     k_link_update<<<grid, kBlock, 0, st>>>(Uin, V, eps, reunit ? 1 : 0, Uout, Wold, dmax, internal ? ctx->u64 : nullptr,
                                            internal ? ctx->u32a : nullptr, internal ? ctx->u32b : nullptr, ctx->g.V); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
-    if (internal) ctx->links_valid = true;
+    if (internal) {
+        ctx->links_valid = true;
+        ctx->link_gen++;
+    }
     return RMHMC_OK;
 }
 
@@ -331,9 +335,10 @@ static bool link_iterates_fp32(const rmhmc_params* p) { return p->prec != RMHMC_
 
 static int link_iter32_launch(rmhmc_ctx* ctx, const double* B, const double* V, double eps, float* W32, bool have_old,
                               double* dmax, cudaStream_t st) {
-    const dim3 grid(site_blocks(ctx), 4);
+    const int grid = lane_blocks(ctx);   // 4 V threads
     k_link_iter32<<<grid, kBlock, 0, st>>>(B, V, (float)eps, W32, have_old ? 1 : 0, dmax, ctx->u32a, ctx->u32b, ctx->g.V);
     ++ctx->launches;
+    ctx->link_gen++;
     RM_LAUNCH_CHECK(ctx);
     return RMHMC_OK;
 }
@@ -381,9 +386,29 @@ static int check_params(rmhmc_ctx* ctx, const rmhmc_params* p) {
     return RMHMC_OK;
 }
 
+// The log|M| term of Eq. (5) through an auxiliary field: phi (fixed in the MD) with action
+// 1/2 <phi, M phi> = 1/2 |Q phi|^2, Q = 1/R as a partial fraction (inv); its force is the kinetic force of phi
+// under Q and joins the gauge force as part of the U-only potential force.
+struct AuxTerm {
+    const double* phi = nullptr;
+    MassTerm inv;
+    double* FA = nullptr;   // scratch force
+    double* VA = nullptr;   // scratch velocity (the captured kinetic evaluation writes one)
+};
+
+// F = F_G(U) (+ F_aux(U) with an auxiliary field) at the context's links
+static int potential_force(rmhmc_ctx* ctx, const rmhmc_params* p, int gprec, const AuxTerm* lg, double* F,
+                           cudaStream_t st) {
+    RM_TRY(gauge_force_launch(ctx, p->beta, p->c1, gprec, F, st));
+    if (!lg) return RMHMC_OK;
+    int it = 0;
+    RM_TRY(kinetic_from_krylov(ctx, lg->inv, lg->phi, p->tol_md, p->maxiter, p->prec, lg->FA, nullptr, nullptr, &it, st));
+    return axpby64(ctx, 1.0, F, 1.0, lg->FA, F, field_elems(ctx), st);
+}
+
 // MD on (U, P) in place.  U canonical device links; the context's links follow U.
 static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, const MassTerm& m, rmhmc_result* r,
-                  cudaStream_t st) {
+                  cudaStream_t st, const AuxTerm* lg = nullptr) {
     MDWork w;
     RM_TRY(md_work(ctx, w));
     const size_t fs = field_elems(ctx), lb = sizeof(double) * (size_t)ctx->g.V * 72;
@@ -393,7 +418,7 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
     long long kiters = 0;
     double worst = 0.0;
     RM_TRY(import_links(ctx, U, st));
-    RM_TRY(gauge_force_launch(ctx, p->beta, p->c1, gprec, w.FG, st));
+    RM_TRY(potential_force(ctx, p, gprec, lg, w.FG, st));
     RM_TRY(mom_update(ctx, P, 0.5 * eps, w.FG, nullptr, nullptr, w.Q, nullptr, st));   // Q0 = P + eps/2 F_G
     for (int step = 0; step < p->nsteps; step++) {
         // (1) momentum fixed point at fixed U
@@ -442,7 +467,7 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
         if (it32) RM_TRY(link_update_launch(ctx, w.B, w.V0, 0.5 * eps, true, U, nullptr, nullptr, true, st));
         else RM_TRY(link_update_launch(ctx, w.W, w.V0, 0.0, true, U, nullptr, nullptr, true, st));
         // (3) explicit half step with F_K(W_i, P') kept from the last iteration
-        RM_TRY(gauge_force_launch(ctx, p->beta, p->c1, gprec, w.FG, st));
+        RM_TRY(potential_force(ctx, p, gprec, lg, w.FG, st));
         RM_TRY(mom_update(ctx, w.Q, 0.5 * eps, w.FG, w.FK, nullptr, P, nullptr, st));
         RM_TRY(mom_update(ctx, P, 0.5 * eps, w.FG, w.FK, nullptr, w.Q, nullptr, st));   // next initial guess
     }
@@ -508,15 +533,24 @@ static std::string md_key(const rmhmc_params* p, const MassTerm& m) {
 }
 
 static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTerm& m, const MDGraphBufs& gb,
-                            const MDWork& w, cudaGraph_t* out) {
+                            const MDWork& w, const AuxTerm* lg, cudaGraph_t* out) {
     cudaStream_t st = ctx->cap_st[0], aux = ctx->cap_st[1], aux2 = ctx->cap_st[2];
     const double eps = p->tau / p->nsteps;
     const int gprec = RMHMC_FP32;
     RM_CHECK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     int s = RMHMC_OK;
     do {
+        // U-only potential force: gauge force, plus the auxiliary-field force as one more captured kinetic
+        // evaluation (its Krylov iterations count with the MD's)
+        auto potential = [&]() -> int {
+            RM_TRY(gauge_force_launch(ctx, p->beta, p->c1, gprec, w.FG, st));
+            if (!lg) return RMHMC_OK;
+            RM_TRY(kinetic_enqueue(ctx, lg->inv, lg->phi, p->tol_md, p->maxiter, lg->FA, lg->VA, gb.stats, gb.ints,
+                                   st, aux2));
+            return axpby64(ctx, 1.0, w.FG, 1.0, lg->FA, w.FG, field_elems(ctx), st);
+        };
         if ((s = import_links(ctx, gb.U, st)) != RMHMC_OK) break;
-        if ((s = gauge_force_launch(ctx, p->beta, p->c1, gprec, w.FG, st)) != RMHMC_OK) break;
+        if ((s = potential()) != RMHMC_OK) break;
         if ((s = mom_update(ctx, gb.P, 0.5 * eps, w.FG, nullptr, nullptr, w.Q, nullptr, st)) != RMHMC_OK) break;
         for (int step = 0; step < p->nsteps && s == RMHMC_OK; step++) {
             // (1) momentum fixed point
@@ -577,7 +611,7 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
             if (it32) s = link_update_launch(ctx, w.B, w.V0, 0.5 * eps, true, gb.U, nullptr, nullptr, true, st);
             else s = link_update_launch(ctx, w.W, w.V0, 0.0, true, gb.U, nullptr, nullptr, true, st);
             if (s != RMHMC_OK) break;
-            if ((s = gauge_force_launch(ctx, p->beta, p->c1, gprec, w.FG, st)) != RMHMC_OK) break;
+            if ((s = potential()) != RMHMC_OK) break;
             if ((s = mom_update(ctx, w.Q, 0.5 * eps, w.FG, w.FK, nullptr, gb.P, nullptr, st)) != RMHMC_OK) break;
             if ((s = mom_update(ctx, gb.P, 0.5 * eps, w.FG, w.FK, nullptr, w.Q, nullptr, st)) != RMHMC_OK) break;
         }
@@ -600,7 +634,7 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
 // Runs the MD through the cached graph; returns RMHMC_OK, a status of the run, or a negative code of the
 // capture (the caller then falls back to the host-driven path)
 static int md_graph_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, const MassTerm& m, rmhmc_result* r,
-                        cudaStream_t stream, bool* used) {
+                        cudaStream_t stream, bool* used, const AuxTerm* lg = nullptr) {
     *used = false;
     if (!ctx->use_graphs || p->prec == RMHMC_FP64 || m.npole() == 0 || 2 * m.npole() + 1 > 32) return RMHMC_OK;
     MDWork w;
@@ -608,9 +642,13 @@ static int md_graph_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params
     MDGraphBufs gb;
     RM_TRY(md_graph_bufs(ctx, gb));
     RM_TRY(kinetic_graph_prepare(ctx, m, p->maxiter));
+    if (lg) {
+        if (lg->inv.npole() == 0 || 2 * lg->inv.npole() + 1 > 32) return RMHMC_OK;
+        RM_TRY(kinetic_graph_prepare(ctx, lg->inv, p->maxiter));
+    }
     for (int i = 0; i < 3; i++)
         if (!ctx->cap_st[i]) RM_CHECK(ctx, cudaStreamCreateWithFlags(&ctx->cap_st[i], cudaStreamNonBlocking));
-    const std::string key = md_key(p, m);
+    const std::string key = md_key(p, m) + (lg ? "|logdet" : "");
     if (!ctx->md_exec || ctx->md_key != key || ctx->md_gen != ctx->ws_gen) {
         if (ctx->md_exec) {
             cudaGraphExecDestroy(ctx->md_exec);
@@ -618,7 +656,7 @@ static int md_graph_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params
         }
         const long long saved = ctx->launches;
         cudaGraph_t g = nullptr;
-        const int s = md_graph_capture(ctx, p, m, gb, w, &g);
+        const int s = md_graph_capture(ctx, p, m, gb, w, lg, &g);
         ctx->launches = saved;
         if (s != RMHMC_OK) {
             ctx->graph_note = "capture failed: " + ctx->err;
@@ -644,6 +682,7 @@ static int md_graph_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params
     RM_CHECK(ctx, cudaMemcpyAsync(gb.P, P, sizeof(double) * fs, cudaMemcpyDeviceToDevice, stream));
     RM_CHECK(ctx, cudaMemsetAsync(gb.stats, 0, 256, stream));
     RM_CHECK(ctx, cudaGraphLaunch(ctx->md_exec, stream));
+    ctx->link_gen++;   // the graph's link updates changed the internal copies
     RM_CHECK(ctx, cudaMemcpyAsync(U, gb.U, lb, cudaMemcpyDeviceToDevice, stream));
     RM_CHECK(ctx, cudaMemcpyAsync(P, gb.P, sizeof(double) * fs, cudaMemcpyDeviceToDevice, stream));
     long long st[4];
@@ -771,18 +810,54 @@ extern "C" int rmhmc_trajectory(rmhmc_ctx* ctx, double* U, const double* xi, con
         return code;
     };
     RM_TRY(import_links(ctx, U, stream));
+    // the log|M| term: phi = R(A) eta with eta from Philox (tag 3), Q = 1/R as a partial fraction
+    AuxTerm lgt;
+    const AuxTerm* lg = nullptr;
+    double* Yaux = nullptr;
+    if (p->logdet) {
+        if (m.npole() == 0) return set_err(ctx, RMHMC_EINVAL, "logdet needs a mass term with poles");
+        double p1 = 0.0;
+        RM_TRY(inverse_rational(ctx, m, lgt.inv, p1));
+        if (p1 != 0.0) return set_err(ctx, RMHMC_EINVAL, "logdet needs c > 0 (1/R without a linear term)");
+        double* phi = (double*)workspace(ctx, "lg_phi", sizeof(double) * fs, &status);
+        double* eta = (double*)workspace(ctx, "lg_eta", sizeof(double) * fs, &status);
+        lgt.FA = (double*)workspace(ctx, "lg_fa", sizeof(double) * fs, &status);
+        lgt.VA = (double*)workspace(ctx, "lg_va", sizeof(double) * fs, &status);
+        Yaux = (double*)workspace(ctx, "lg_y", sizeof(double) * fs, &status);
+        if (!phi || !eta || !lgt.FA || !lgt.VA || !Yaux) return status;
+        k_gauss_field<<<site_blocks(ctx), kBlock, 0, stream>>>(eta, ctx->g.V, p->seed, p->traj_index, 3u); ++ctx->launches;
+        RM_LAUNCH_CHECK(ctx);
+        int s0 = rational_apply(ctx, m, eta, p->tol_h, p->maxiter, p->prec, phi, nullptr, stream);
+        if (s0 != RMHMC_OK) return restore(s0);
+        lgt.phi = phi;
+        lg = &lgt;
+    }
+    // auxiliary action 1/2 |Q phi|^2 at the context's links
+    auto aux_action = [&](double* A) -> int {
+        *A = 0.0;
+        if (!lg) return RMHMC_OK;
+        RM_TRY(rational_apply(ctx, lg->inv, lg->phi, p->tol_h, p->maxiter, p->prec, Yaux, nullptr, stream));
+        double y2 = 0.0;
+        RM_TRY(norm2_64(ctx, Yaux, fs, &y2, stream));
+        *A = 0.5 * y2;
+        return isfinite(*A) ? RMHMC_OK : set_err(ctx, RMHMC_ENAN, "NaN/Inf in the auxiliary action");
+    };
     // the heatbath at the Hamiltonian's tolerance: mixed and float64 trajectories from the same noise then
     // start from the same momenta
     int s = heatbath_apply(ctx, m, X, p->tol_h, p->maxiter, p->prec, P, stream);
     if (s != RMHMC_OK) return restore(s);
     s = hamiltonian_run(ctx, U, P, p, m, &res.H0, &res.T0, &res.S0, nullptr, stream);
+    if (s == RMHMC_OK) s = aux_action(&res.A0);
     if (s != RMHMC_OK) return restore(s);
     bool used = false;
-    s = md_graph_run(ctx, U, P, p, m, &res, stream, &used);
-    if (s == RMHMC_OK && !used) s = md_run(ctx, U, P, p, m, &res, stream);
+    s = md_graph_run(ctx, U, P, p, m, &res, stream, &used, lg);
+    if (s == RMHMC_OK && !used) s = md_run(ctx, U, P, p, m, &res, stream, lg);
     if (s != RMHMC_OK) return restore(s);
     s = hamiltonian_run(ctx, U, P, p, m, &res.H1, &res.T1, &res.S1, &res.plaq, stream);
+    if (s == RMHMC_OK) s = aux_action(&res.A1);
     if (s != RMHMC_OK) return restore(s);
+    res.H0 += res.A0;
+    res.H1 += res.A1;
     res.dH = res.H1 - res.H0;
     res.u = philox_uniform(p->seed, p->traj_index, 1u);
     res.accepted = (!p->metropolis || res.dH <= 0.0 || res.u <= exp(-res.dH)) ? 1 : 0;

@@ -136,6 +136,70 @@ static void launch_cg_A(rmhmc_ctx* ctx, const StencilShape& shp, typename LinksO
     ++ctx->launches;
 }
 
+// Launch shape of the CG stencil, tuned on its own (its loads differ from the plain stencil's: it also reads
+// and writes q, and the one-component shape reads the basis with 256-bit loads): every shape is timed on the
+// context's lattice (k = 0 on zeroed scratch, three repetitions after a warm-up) at first use.
+template <typename T>
+static int cg_shape(rmhmc_ctx* ctx, cudaStream_t st, StencilShape& out) {
+    const int key = 10000 + (int)sizeof(T) * 100 + 18;
+    auto it = ctx->tune.find(key);
+    if (it != ctx->tune.end()) {
+        out.nmu = it->second.first;
+        out.block = it->second.second;
+        return RMHMC_OK;
+    }
+    StencilShape base;
+    RM_TRY((stencil_shape<T, 18>(ctx, st, base)));
+    int status = RMHMC_OK;
+    const size_t fs = field_elems(ctx);
+    T* X = (T*)workspace(ctx, "tune_x", sizeof(double) * fs, &status);
+    T* Y = (T*)workspace(ctx, "tune_y", sizeof(double) * fs, &status);
+    int* flags = (int*)workspace(ctx, "tune_cgflags", 64, &status);
+    double* vals = (double*)workspace(ctx, "tune_cgvals", 64, &status);
+    if (!X || !Y || !flags || !vals) return status;
+    RM_CHECK(ctx, cudaMemsetAsync(X, 0, sizeof(T) * fs, st));
+    RM_CHECK(ctx, cudaMemsetAsync(flags, 0, 64, st));
+    RM_CHECK(ctx, cudaMemsetAsync(vals, 0, 64, st));
+    typename LinksOf<T>::type U;
+    if constexpr (sizeof(T) == 8) U = links64(ctx); else U = links32(ctx);
+    cudaEvent_t e0, e1;
+    RM_CHECK(ctx, cudaEventCreate(&e0));
+    RM_CHECK(ctx, cudaEventCreate(&e1));
+    float best = 1e30f;
+    StencilShape bs;
+    char line[128];
+    std::string rep;
+    for (int nmu : {1, 2, 4, 0})
+        for (int block : {64, 128, 256}) {
+            const StencilShape shp{nmu, block};
+            auto run = [&]() {
+                if (nmu == 4) launch_cg_A<T, 4>(ctx, shp, U, X, fs, Y, T(1), flags, vals, 1, st);
+                else if (nmu == 2) launch_cg_A<T, 2>(ctx, shp, U, X, fs, Y, T(1), flags, vals, 1, st);
+                else if (nmu == 0) launch_cg_A<T, 0>(ctx, shp, U, X, fs, Y, T(1), flags, vals, 1, st);
+                else launch_cg_A<T, 1>(ctx, shp, U, X, fs, Y, T(1), flags, vals, 1, st);
+            };
+            run();
+            RM_CHECK(ctx, cudaEventRecord(e0, st));
+            for (int r = 0; r < 3; r++) run();
+            RM_CHECK(ctx, cudaEventRecord(e1, st));
+            RM_CHECK(ctx, cudaEventSynchronize(e1));
+            RM_LAUNCH_CHECK(ctx);
+            float ms = 0.f;
+            RM_CHECK(ctx, cudaEventElapsedTime(&ms, e0, e1));
+            ms /= 3.f;
+            snprintf(line, sizeof line, "%s%d/%d:%.4f", rep.empty() ? "" : " ", nmu, block, ms);
+            rep += line;
+            if (ms < best) { best = ms; bs = shp; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tune[key] = {bs.nmu, bs.block};
+    snprintf(line, sizeof line, "; cg %s -> nmu %d block %d [", sizeof(T) == 8 ? "fp64" : "fp32", bs.nmu, bs.block);
+    ctx->tune_report += line + rep + "]";
+    out = bs;
+    return RMHMC_OK;
+}
+
 // r_{k+1} = r_k - alpha_k q_k ; rho_{k+1} = |r_{k+1}|^2 ; beta_k ; convergence flags; k advances
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_B(T* __restrict__ R, size_t fs, const T* __restrict__ q, size_t nvec,
@@ -439,7 +503,7 @@ int krylov_run(rmhmc_ctx* ctx, const T* b, double sigma0, double tol, int maxit,
     T* R = (T*)w.basis;
     const int nb = capped_grid(ctx, nvec, kBlock);
     StencilShape shp;
-    RM_TRY((stencil_shape<T, 18>(ctx, st, shp)));
+    RM_TRY(cg_shape<T>(ctx, st, shp));
     k_cg_start<T><<<nb, kBlock, 0, st>>>(b, R, nvec, w.flags, w.vals, red_slot_partials(ctx, kSlotRho),
                                          red_slot_counter(ctx, kSlotRho)); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
@@ -724,12 +788,89 @@ int rational_apply(rmhmc_ctx* ctx, const MassTerm& m, const double* b, double to
     return RMHMC_OK;
 }
 
+// 1/R(lam) = p0 + p1 lam + sum_j beta_j / (lam + zeta_j) for R = c + sum_j alpha_j / (lam + sigma_j) with c >= 0,
+// alpha_j >= 0 (terms with alpha_j = 0 dropped).  R has one zero between consecutive poles and, when c > 0, one
+// below the smallest -sigma; each is bracketed and bisected in long double; beta_j = 1 / R'(-zeta_j).  At
+// infinity 1/R -> 1/c (c > 0), else lam / sum(alpha) + sum(alpha sigma) / sum(alpha)^2.
+int inverse_rational(rmhmc_ctx* ctx, const MassTerm& m, MassTerm& inv, double& p1) {
+    typedef long double ld;
+    std::vector<std::pair<double, double>> t;   // (sigma, alpha)
+    for (int j = 0; j < m.npole(); j++) {
+        if (m.alpha[j] < 0.0) return set_err(ctx, RMHMC_EINVAL, "general rational mass: alpha_j must be >= 0");
+        if (m.alpha[j] > 0.0) t.push_back({m.sigma[j], m.alpha[j]});
+    }
+    if (m.c < 0.0 || (m.c == 0.0 && t.empty())) return set_err(ctx, RMHMC_EINVAL, "general rational mass: R is not positive");
+    std::sort(t.begin(), t.end());
+    const int n = (int)t.size();
+    auto R = [&](ld x) {
+        ld r = (ld)m.c;
+        for (const auto& q : t) r += (ld)q.second / (x + (ld)q.first);
+        return r;
+    };
+    auto bisect = [&](ld lo, ld hi) {   // R(lo) > 0 > R(hi)
+        for (int i = 0; i < 300 && hi - lo > 0; i++) {
+            const ld mid = 0.5L * (lo + hi);
+            if (mid == lo || mid == hi) break;
+            if (R(mid) > 0) lo = mid; else hi = mid;
+        }
+        return 0.5L * (lo + hi);
+    };
+    std::vector<ld> zeros;
+    for (int j = 0; j + 1 < n; j++) zeros.push_back(bisect(-(ld)t[j + 1].first, -(ld)t[j].first));
+    if (m.c > 0.0 && n > 0) {
+        const ld hi = -(ld)t[n - 1].first;
+        ld d = 1.0L;
+        int guard = 0;
+        while (R(hi - d) <= 0 && guard++ < 400) d *= 2.0L;
+        zeros.push_back(bisect(hi - d, hi));
+    }
+    inv.kappa = 0.0;
+    inv.alpha.clear();
+    inv.sigma.clear();
+    for (ld z : zeros) {
+        ld dr = 0.0L;
+        for (const auto& q : t) dr -= (ld)q.second / ((z + (ld)q.first) * (z + (ld)q.first));
+        inv.alpha.push_back((double)(1.0L / dr));
+        inv.sigma.push_back((double)(-z));
+    }
+    if (m.c > 0.0) {
+        inv.c = 1.0 / m.c;
+        p1 = 0.0;
+    } else {
+        ld sa = 0.0L, sas = 0.0L;
+        for (const auto& q : t) { sa += (ld)q.second; sas += (ld)q.second * (ld)q.first; }
+        inv.c = (double)(sas / (sa * sa));
+        p1 = (double)(1.0L / sa);
+    }
+    return RMHMC_OK;
+}
+
 int heatbath_apply(rmhmc_ctx* ctx, const MassTerm& m, const double* xi, double tol, int maxiter, int prec, double* P,
                    cudaStream_t st) {
     int status = RMHMC_OK;
     const size_t fs = field_elems(ctx);
     double* y = (double*)workspace(ctx, "hb_y", sizeof(double) * fs, &status);
     if (!y) return status;
+    if (m.kappa == 0.0 && m.npole() > 0) {
+        // general rational mass M = R^{-2}: P = R(A)^{-1} xi exactly, from the partial fraction of 1/R
+        MassTerm inv;
+        double p1 = 0.0;
+        RM_TRY(inverse_rational(ctx, m, inv, p1));
+        RM_TRY(rational_apply(ctx, inv, xi, tol, maxiter, prec, y, nullptr, st));
+        if (p1 == 0.0) {
+            RM_CHECK(ctx, cudaMemcpyAsync(P, y, sizeof(double) * fs, cudaMemcpyDeviceToDevice, st));
+            return RMHMC_OK;
+        }
+        // P = y + p1 A xi = y + p1 (xi / 2 - H(xi) / 16) (through scratch when P is xi itself)
+        double* out = P;
+        if (P == xi) {
+            out = (double*)workspace(ctx, "hb_t", sizeof(double) * fs, &status);
+            if (!out) return status;
+        }
+        RM_TRY(launch_lap(ctx, RMHMC_FP64, 18, xi, out, 1, 0.5 * p1, -p1 / 16.0, y, 1.0, -1, st));
+        if (out != P) RM_CHECK(ctx, cudaMemcpyAsync(P, out, sizeof(double) * fs, cudaMemcpyDeviceToDevice, st));
+        return RMHMC_OK;
+    }
     RM_TRY(rational_apply(ctx, m, xi, tol, maxiter, prec, y, nullptr, st));
     // P = (1-kappa) y + kappa A y = ((1-kappa) + kappa/2) y - (kappa/16) H(y)
     const double k = m.kappa;
@@ -962,7 +1103,7 @@ int kinetic_graph_prepare(rmhmc_ctx* ctx, const MassTerm& m, int maxiter) {
     KinGraphBufs b;
     RM_TRY(kin_graph_bufs(ctx, m.npole(), maxiter, b));
     StencilShape shp;
-    return stencil_shape<float, 18>(ctx, 0, shp);
+    return cg_shape<float>(ctx, 0, shp);
 }
 
 // Enqueue (on a capturing stream) one mixed-precision kinetic evaluation at the context's links:
@@ -979,7 +1120,7 @@ int kinetic_enqueue(rmhmc_ctx* ctx, const MassTerm& m, const double* P, double t
     const size_t nvec = fs / 4;
     const int nb = capped_grid(ctx, nvec, kBlock);
     StencilShape shp;
-    RM_TRY((stencil_shape<float, 18>(ctx, st, shp)));
+    RM_TRY(cg_shape<float>(ctx, st, shp));
     const double s0 = *std::min_element(m.sigma.begin(), m.sigma.end());
     DevMass dm{};
     dm.ns = ns;

@@ -100,6 +100,8 @@ int kinetic_graph_prepare(rmhmc_ctx* ctx, const MassTerm& m, int maxiter);
 int kinetic_enqueue(rmhmc_ctx* ctx, const MassTerm& m, const double* P, double tol, int maxiter, double* F, double* Vel,
                     long long* stats, int* status, cudaStream_t st, cudaStream_t aux);
 
+// 1/R(lam) = inv.c + p1 lam + sum_j inv.alpha_j / (lam + inv.sigma_j) for a mass term with c >= 0, alpha_j >= 0
+int inverse_rational(rmhmc_ctx* ctx, const MassTerm& m, MassTerm& inv, double& p1);
 // momentum heatbath P = m(A) R(A) xi, m(A) = (1-kappa) + kappa A (float64 in and out)
 int heatbath_apply(rmhmc_ctx* ctx, const MassTerm& m, const double* xi, double tol, int maxiter, int prec, double* P,
                    cudaStream_t st);

@@ -186,12 +186,17 @@ __global__ void __launch_bounds__(kBlock) k_norm2_fields(const float* __restrict
 
 int adjoint_table(rmhmc_ctx* ctx, float** tab, cudaStream_t st) {
     int status = RMHMC_OK;
+    const unsigned long long ws = ctx->ws_gen;
     float* t = (float*)workspace(ctx, "rd_adjoint", sizeof(float) * (size_t)ctx->g.V * 4 * 128, &status);
     if (!t) return status;
+    *tab = t;
+    // the table of the current links is kept until they change (a heatbath and the Hamiltonian that follows
+    // share it)
+    if (ctx->adj_gen == ctx->link_gen && ws == ctx->ws_gen) return RMHMC_OK;
     const dim3 grid(site_blocks(ctx), 4);
     k_adjoint_table<<<grid, kBlock, 0, st>>>(links64(ctx), ctx->g.V, t); ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
-    *tab = t;
+    ctx->adj_gen = ctx->link_gen;
     return RMHMC_OK;
 }
 

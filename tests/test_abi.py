@@ -23,7 +23,7 @@ def declared_functions():
 def test_header_declares_the_entry_points():
     names = declared_functions()
     for n in ["lap_apply", "cheb_filter_spectrum", "rat_mass_solve", "gauge_force", "kinetic_force",
-              "rmhmc_trajectory", "rmhmc_create", "rmhmc_destroy"]:
+              "rmhmc_trajectory", "rmhmc_create", "rmhmc_destroy", "wilson_flow"]:
         assert n in names
 
 
@@ -38,5 +38,5 @@ def test_library_exports_every_declared_symbol():
 def test_binding_names_match():
     import paper_2112_04556_gb300 as rm
     for n in ["lap_apply", "cheb_filter_spectrum", "rat_mass_solve", "gauge_force", "kinetic_force",
-              "rmhmc_trajectory", "lap_link_grad", "heatbath", "mass_fit"]:
+              "rmhmc_trajectory", "lap_link_grad", "heatbath", "mass_fit", "wilson_flow"]:
         assert callable(getattr(rm, n))

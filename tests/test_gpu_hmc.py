@@ -151,3 +151,52 @@ def test_trajectory_errors_leave_links_unchanged():
         assert np.abs(host(Ud) - U).max() == 0.0
         with pytest.raises(rm.RmhmcError):
             rm.rmhmc_trajectory(ctx, Ud, _params(rm, rm.mass_fit(12, 0.9), nsteps=0))
+
+
+def _logdet_params(rm, m, prec, **kw):
+    d = dict(beta=6.0, c1=0.0, mass=m, tau=0.2, nsteps=4, tol_md=1e-13 if prec == 0 else 1e-6,
+             tol_h=1e-13 if prec == 0 else 1e-12, fp_tol=1e-13 if prec == 0 else 1e-6, fp_maxit=100,
+             maxiter=2000, prec=prec, seed=5, traj_index=2, metropolis=False, logdet=True)
+    d.update(kw)
+    return rm.make_params(**d)
+
+
+def test_logdet_trajectory_parity():
+    """The log|M| term through the auxiliary field: float64 trajectory against the oracle's with the same
+    Philox noise (xi tag 0, eta tag 3); A0 = |eta|^2 / 2."""
+    import paper_2112_04556_gb300 as rm
+    L = (4, 4, 4, 4)
+    U = inputs.random_links(L, eps=0.3, seed=65)
+    m = fit.mass_term(8, 0.9)
+    xi = oracle.gauss_field(L, 5, 2, 0)
+    eta = oracle.gauss_field(L, 5, 2, 3)
+    ref = oracle.trajectory(L, U, xi, oracle.uniform(5, 2), 0.2, 4, 6.0, 0.0, m, tol_md=1e-13, tol_h=1e-13,
+                            fp_tol=1e-13, metropolis=False, eta=eta)
+    with rm.Context(L) as ctx:
+        Ud = dev(U)
+        r = rm.rmhmc_trajectory(ctx, Ud, _logdet_params(rm, m, rm.FP64))
+        Uo = host(Ud)
+    assert abs(r["A0"] - 0.5 * np.sum(eta * eta)) <= 1e-10 * r["A0"]
+    assert abs(r["A0"] - ref["A0"]) <= 1e-10 * ref["A0"] and abs(r["A1"] - ref["A1"]) <= 1e-10 * ref["A1"]
+    assert abs(r["dH"] - ref["dH"]) <= 1e-8
+    assert np.abs(Uo - ref["U1"]).max() <= 1e-10
+
+
+def test_logdet_mixed_graph_and_host_agree_with_fp64():
+    """8^4: the mixed trajectory with the auxiliary field, captured as a graph and host-driven, against
+    float64 (small step: dH = O(1e-2))."""
+    import paper_2112_04556_gb300 as rm
+    L = (8, 8, 8, 8)
+    U = inputs.random_links(L, eps=0.3, seed=66)
+    m = rm.mass_fit(12, 0.9)
+    out = {}
+    with rm.Context(L) as ctx:
+        out["fp64"] = rm.rmhmc_trajectory(ctx, dev(U), _logdet_params(rm, m, rm.FP64, tol_md=1e-10, fp_tol=1e-10))
+        out["graph"] = rm.rmhmc_trajectory(ctx, dev(U), _logdet_params(rm, m, rm.MIXED))
+        note = rm.tuning(ctx)
+        rm.set_graphs(ctx, False)
+        out["host"] = rm.rmhmc_trajectory(ctx, dev(U), _logdet_params(rm, m, rm.MIXED))
+    assert "md graph captured" in note
+    assert abs(out["graph"]["dH"] - out["host"]["dH"]) <= 1e-6
+    assert abs(out["graph"]["dH"] - out["fp64"]["dH"]) <= 1e-3
+    assert abs(out["fp64"]["A0"] - out["graph"]["A0"]) <= 1e-9 * out["fp64"]["A0"]

@@ -105,3 +105,55 @@ def test_solve_errors():
         z = b * 0
         y, _, iters, resid = rm.rat_mass_solve(ctx, Ud, z, rm.mass_fit(12, 0.9))
         assert iters == 0 and float(y.abs().max()) == 0.0
+
+
+def _fitted_mass():
+    lam = (np.arange(64) + 0.5) / 64
+    return fit.spectrum_mass_term(lam, 0.05 + lam ** 1.2, 8)
+
+
+def test_general_heatbath_parity():
+    """A mass fitted to a spectrum (kappa = 0): P = R(A)^{-1} xi from the library's inverse partial
+    fraction against the oracle's CG on R(A); T(P) = |xi|^2 / 2."""
+    import paper_2112_04556_gb300 as rm
+    L = (4, 4, 4, 4)
+    U = inputs.random_links(L, eps=0.4, seed=27)
+    xi = inputs.gaussian_fields(L, 1, seed=28)[0]
+    m = _fitted_mass()
+    ref = oracle.heatbath(L, U, xi, m, tol=1e-13)
+    with rm.Context(L) as ctx:
+        P = rm.heatbath(ctx, dev(U), dev(xi), m, tol=1e-13, prec=rm.FP64)
+        assert rel_l2(host(P), ref) <= 1e-11
+        Pm = rm.heatbath(ctx, None, dev(xi), m, tol=1e-11, prec=rm.MIXED)
+        assert rel_l2(host(Pm), ref) <= 1e-9
+        _, _, T = rm.kinetic_force(ctx, None, P, m, tol=1e-13, prec=rm.FP64)
+    assert abs(T - 0.5 * np.sum(xi * xi)) <= 1e-10 * T
+
+
+def test_spectrum_fitted_mass_trajectory():
+    """The loop of Sec. 4 on 8^4: the Wilson-force spectrum, a mass fitted to it, and a trajectory with that
+    mass whose H0 = |xi|^2 / 2 + S0 (exact heatbath); float64 and mixed agree."""
+    import paper_2112_04556_gb300 as rm
+    import torch
+    L = (8, 8, 8, 8)
+    U = inputs.random_links(L, eps=0.3, seed=29)
+    edges = inputs.equal_windows(16)
+    with rm.Context(L) as ctx:
+        Ud = dev(U)
+        F, _, _ = rm.gauge_force(ctx, Ud, 6.0, 0.0, prec=rm.FP64)
+        spec = rm.cheb_filter_spectrum(ctx, None, F[None], None, 64, edges, prec=rm.FP64, nnoise=16, seed=3)[0][0]
+        lam = 0.5 * (edges[:-1] + edges[1:])
+        ok = spec > 1e-6 * spec.max()
+        m = rm.mass_fit_spectrum(lam[ok], spec[ok], 8)
+        # a noisy measured spectrum need not be monotone, the fitted mass always is: R > 0 decreasing
+        R = fit.evaluate(m, np.linspace(0.0, 1.0, 101))
+        assert np.isfinite(m["err"]) and np.all(R > 0) and np.all(np.diff(R) < 0)
+        xi = torch.from_numpy(inputs.gaussian_fields(L, 1, seed=30)[0]).cuda()
+        out = {}
+        for prec in (rm.FP64, rm.MIXED):
+            p = rm.make_params(beta=6.0, mass=m, tau=0.1, nsteps=4, tol_md=1e-10 if prec == 0 else 1e-6, tol_h=1e-12,
+                               fp_tol=1e-10 if prec == 0 else 1e-6, prec=prec, metropolis=False)
+            out[prec] = rm.rmhmc_trajectory(ctx, dev(U), p, xi=xi)
+    r = out[rm.FP64]
+    assert abs(r["T0"] - 0.5 * float((xi * xi).sum())) <= 1e-9 * r["T0"]
+    assert np.isfinite(r["dH"]) and abs(out[rm.MIXED]["dH"] - r["dH"]) <= 1e-2 * max(1.0, abs(r["dH"]))

@@ -44,3 +44,68 @@ def test_fit_arguments():
     assert _fit(L, 25, 0.9)[0] == -1
     code, c, _, _, e = _fit(L, 0, 0.0)
     assert code == 0 and c == 1.0 and e == 0.0
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_window_coefficients_match_oracle(kernel):
+    """cheb_window_coeffs (host C++) against the oracle's numpy expansion of the window indicators."""
+    import oracle
+    lib = _lib()
+    edges = np.array([0.0, 0.05, 0.2, 0.5, 0.51, 1.0])
+    N = 150
+    C = np.zeros((len(edges) - 1, N + 1))
+    P = ctypes.POINTER(ctypes.c_double)
+    rc = lib.cheb_window_coeffs(ctypes.c_int(len(edges) - 1), edges.ctypes.data_as(P), ctypes.c_int(N),
+                                ctypes.c_int(kernel), C.ctypes.data_as(P))
+    assert rc == 0
+    ref = oracle.window_coeffs(edges, N, kernel="jackson" if kernel == 1 else "none")
+    assert np.abs(C - ref).max() < 1e-14
+    bad = np.array([0.0, 0.5, 0.4])
+    assert lib.cheb_window_coeffs(ctypes.c_int(2), bad.ctypes.data_as(P), ctypes.c_int(N), ctypes.c_int(1),
+                                  C.ctypes.data_as(P)) == -1
+
+
+def _spec_fit(lam, spec, npole, smin=1e-3, smax=10.0):
+    lib = _lib()
+    P = ctypes.POINTER(ctypes.c_double)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    spec = np.ascontiguousarray(spec, dtype=np.float64)
+    c = ctypes.c_double()
+    err = ctypes.c_double()
+    alpha = np.zeros(npole)
+    sigma = np.zeros(npole)
+    rc = lib.rmhmc_mass_fit_spectrum(ctypes.c_int(len(lam)), lam.ctypes.data_as(P), spec.ctypes.data_as(P),
+                                     ctypes.c_int(npole), ctypes.c_double(smin), ctypes.c_double(smax),
+                                     ctypes.byref(c), alpha.ctypes.data_as(P), sigma.ctypes.data_as(P),
+                                     ctypes.byref(err))
+    return rc, {"c": c.value, "alpha": alpha, "sigma": sigma, "kappa": 0.0}, err.value
+
+
+@pytest.mark.parametrize("shape", ["rational", "linear", "curved"])
+def test_spectrum_fit_matches_oracle(shape):
+    """rmhmc_mass_fit_spectrum (host C++, its own Lawson-Hanson NNLS) against the oracle's scipy NNLS fit:
+    the fitted R agrees at the windows and on [0, 1]."""
+    lam = (np.arange(64) + 0.5) / 64
+    if shape == "rational":
+        s = 5.0 * fit.evaluate({"c": 0.3, "alpha": np.array([0.01, 0.0, 0.2, 0.05, 0.0, 0.3, 0.0, 0.4]),
+                                "sigma": np.geomspace(1e-3, 10.0, 8)}, lam) ** -2
+    elif shape == "linear":
+        s = 0.1 + lam
+    else:
+        s = 0.05 + lam ** 1.3 + 0.2 * np.sin(3 * lam) ** 2
+    rc, m, err = _spec_fit(lam, s, 8)
+    assert rc == 0
+    ref = fit.spectrum_mass_term(lam, s, 8)
+    assert np.abs(m["sigma"] - ref["sigma"]).max() < 1e-14 * 10
+    grid = np.linspace(0.0, 1.0, 101)
+    assert np.abs(fit.evaluate(m, grid) / fit.evaluate(ref, grid) - 1).max() < 1e-8
+    assert abs(err - ref["err"]) < 1e-8 + 1e-6 * ref["err"]
+    assert m["c"] >= 0 and np.all(m["alpha"] >= 0)
+
+
+def test_spectrum_fit_arguments():
+    lam = np.array([0.1, 0.5, 0.9])
+    assert _spec_fit(lam, np.array([1.0, -1.0, 2.0]), 4)[0] == -1
+    assert _spec_fit(np.array([0.1, 1.5, 0.9]), np.ones(3), 4)[0] == -1
+    assert _spec_fit(lam, np.ones(3), 25)[0] == -1
+    assert _spec_fit(lam, np.ones(3), 4, smin=0.0)[0] == -1
