@@ -248,6 +248,9 @@ def main():
     ap.add_argument("--therm", type=int, default=20, help="plain-HMC thermalisation trajectories")
     ap.add_argument("--graphs", choices=["on", "off"], default="on",
                     help="run the mixed-precision MD as one CUDA graph per trajectory")
+    ap.add_argument("--no-parity", action="store_true", help="skip the small-step float64-vs-mixed dH parity pair")
+    ap.add_argument("--compare-tau", type=float, default=TAU,
+                    help="trajectory length of the float64-vs-mixed comparison (same number of steps)")
     args = ap.parse_args()
     global DIMS
     DIMS = tuple(int(v) for v in args.dims.split(","))
@@ -291,8 +294,8 @@ def main():
                            prec=rm.MIXED, seed=seeds["therm"], traj_index=1000 + n, metropolis=False)
         therm.append(rm.rmhmc_trajectory(lat, U, p)["plaq"])
 
-    def params(idx, prec):
-        return rm.make_params(beta=BETA, mass=mass, tau=TAU, nsteps=args.nsteps,
+    def params(idx, prec, tau=TAU):
+        return rm.make_params(beta=BETA, mass=mass, tau=tau, nsteps=args.nsteps,
                               tol_md=1e-6 if prec == rm.MIXED else 1e-10, tol_h=1e-12,
                               fp_tol=1e-6 if prec == rm.MIXED else 1e-10, fp_maxit=50, maxiter=400, prec=prec,
                               seed=seeds["traj"], traj_index=idx, metropolis=True)
@@ -378,13 +381,30 @@ def main():
     if world == 1 and not args.no_fp64:
         Ua, Ub = U_start.clone(), U_start.clone()
         t0 = time.perf_counter()
-        ra = rm.rmhmc_trajectory(lat, Ua, params(0, rm.FP64))
+        ra = rm.rmhmc_trajectory(lat, Ua, params(0, rm.FP64, args.compare_tau))
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
-        rb = rm.rmhmc_trajectory(lat, Ub, params(0, rm.MIXED))
-        fp64 = {"traj_per_s_fp64": 1.0 / t64, "dH_fp64": ra["dH"], "dH_mixed": rb["dH"],
+        rb = rm.rmhmc_trajectory(lat, Ub, params(0, rm.MIXED, args.compare_tau))
+        fp64 = {"tau": args.compare_tau, "nsteps": args.nsteps,
+                "traj_per_s_fp64": 1.0 / t64, "dH_fp64": ra["dH"], "dH_mixed": rb["dH"],
                 "abs_dH_diff": abs(ra["dH"] - rb["dH"]), "plaq_fp64": ra["plaq"], "plaq_mixed": rb["plaq"],
                 "md_iters_fp64": ra["md_iters"], "md_iters_mixed": rb["md_iters"]}
+        # the |dH| parity of the mixed path where dH = O(0.1): tau = 0.1 in the same 20 steps, mixed forces to
+        # 3e-7 and fixed points to 1e-8 (float32 forces allow no tighter fixed points at this step size)
+        if not args.no_parity:
+            def pp(prec, tol_md, fp_tol):
+                return rm.make_params(beta=BETA, mass=mass, tau=0.1, nsteps=args.nsteps, tol_md=tol_md, tol_h=1e-12,
+                                      fp_tol=fp_tol, fp_maxit=50, maxiter=400, prec=prec, seed=seeds["traj"],
+                                      traj_index=0, metropolis=False)
+            Ua, Ub = U_start.clone(), U_start.clone()
+            ra = rm.rmhmc_trajectory(lat, Ua, pp(rm.FP64, 1e-10, 1e-10))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rb = rm.rmhmc_trajectory(lat, Ub, pp(rm.MIXED, 3e-7, 1e-8))
+            torch.cuda.synchronize()
+            fp64["small_step"] = {"tau": 0.1, "nsteps": args.nsteps, "mixed_tol_md": 3e-7, "mixed_fp_tol": 1e-8,
+                                  "dH_fp64": ra["dH"], "dH_mixed": rb["dH"], "abs_dH_diff": abs(ra["dH"] - rb["dH"]),
+                                  "mixed_seconds": time.perf_counter() - t0}
 
     if rank != 0:
         return 0
