@@ -40,3 +40,14 @@ def test_binding_names_match():
     for n in ["lap_apply", "cheb_filter_spectrum", "rat_mass_solve", "gauge_force", "kinetic_force",
               "rmhmc_trajectory", "lap_link_grad", "heatbath", "mass_fit", "wilson_flow"]:
         assert callable(getattr(rm, n))
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without librmhmc.so every entry point raises instead of computing elsewhere."""
+    import paper_2112_04556_gb300 as rm
+    monkeypatch.setattr(rm, "_SO", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(rm, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        rm.lib()
+    with pytest.raises(RuntimeError):
+        rm.window_coeffs([0.0, 1.0], 4)
