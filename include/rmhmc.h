@@ -79,8 +79,10 @@ typedef struct rmhmc_ctx rmhmc_ctx;
  *   R(lam) = c + sum_{j<npole} alpha[j] / (lam + sigma[j]),  sigma[j] > 0,
  * the partial-fraction form of the bracket of Eq. (6) (each quadratic denominator of Eq. 6 gives two
  * simple poles).  kappa is the slope of the target linear mass m(lam) = (1-kappa) + kappa*lam used by
- * the momentum heatbath P = m(A) R(A) xi (= M^{1/2} xi to the accuracy of the fit).  npole = 0 and
- * c = 1 give M = 1 (plain HMC).  alpha and sigma are host arrays. */
+ * the momentum heatbath P = m(A) R(A) xi (= M^{1/2} xi to the accuracy of the fit).  kappa = 0 with
+ * poles marks a general rational mass (e.g. from rmhmc_mass_fit_spectrum; c >= 0, alpha >= 0), whose
+ * heatbath is P = R(A)^{-1} xi exactly.  npole = 0 and c = 1 give M = 1 (plain HMC).  alpha and sigma
+ * are host arrays. */
 typedef struct {
     double c;
     int npole;
