@@ -310,8 +310,9 @@ int rmhmc_md(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, rmhmc_
 
 /* One RMHMC trajectory on U in place: heatbath P0 = m(A)R(A) xi (xi device float64 [V][4][8], or
  * NULL: Philox(seed, traj_index, tag 0)), H0, MD, H1, then Metropolis with the uniform from Philox
- * (seed, traj_index, tag 1) unless p->metropolis == 0.  On rejection U is restored.  P_out
- * (device, nullable) receives the final momenta of the MD. */
+ * (seed, traj_index, tag 1) unless p->metropolis == 0.  With p->logdet the auxiliary field of the log|M|
+ * term is drawn (Philox tag 3), its action enters H0 and H1 (r->A0, r->A1) and its force the MD.  On
+ * rejection U is restored.  P_out (device, nullable) receives the final momenta of the MD. */
 int rmhmc_trajectory(rmhmc_ctx* ctx, double* U, const double* xi, const rmhmc_params* p,
                      rmhmc_result* r, double* P_out, cudaStream_t stream);
 
