@@ -7,8 +7,14 @@ mixed precision (float32 Krylov, float64 link update, reductions and Hamiltonian
 trajectory followed by the per-mode power spectrum of the new configuration's Wilson and Iwasaki
 gauge forces (degree-200 Chebyshev filters over 64 windows, 16 noise vectors, one batched launch per
 recurrence step).  Links: seeded random start exp(i 0.3 sum r_a T_a), thermalised by plain HMC before
-timing.  Every input is synthetic; the working set (~30 GB) exceeds the 126 MB L2, so no flush is
+timing.  Every input is synthetic; the working set (~30 GB) exceeds the 129 MB L2, so no flush is
 needed between steps.
+
+Besides the timed steps the line carries: the roofline of the CG stencil (CUDA events around its
+launches in the host-driven solves; DRAM traffic from an ncu capture of the same launch shape), the
+same steps through host buffers (e2e), one float64 and one mixed trajectory from the same links and
+momenta at tau = 1 and at tau = 0.1 with tight mixed tolerances (fp64_compare), SM clocks sampled
+during the timed region, and the float64 CPU oracle on a bounded sample (cpu_baseline).
 
 Prints one JSON line (rank 0).  --impl reference times the float64 CPU oracle instead.
 """
