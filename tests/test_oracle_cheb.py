@@ -161,3 +161,24 @@ def test_filter_apply_free_plane_wave_and_partition(oracle_lib):
         assert np.abs(Y - npcheb.chebval(2 * lam - 1, C[w]) * X).max() < 1e-12
         total += Y
     assert np.abs(total - X).max() < 1e-12
+
+
+def test_heatbath_momenta_spectrum_is_the_mass(oracle_lib):
+    """The per-mode spectrum of heatbath momenta P = M^{1/2} xi is M itself: on random links, with the
+    Zolotarev mass m(lam) = (1-kappa) + kappa lam, the window spectra of P follow m at the window centres
+    (Eq. 4 normalisation; Hutchinson noise and the momenta from independent Gaussians)."""
+    from oracle import fit
+    L = (4, 4, 4, 4)
+    U = inputs.random_links(L, eps=0.3, seed=60)
+    m = fit.mass_term(12, 0.9)
+    xis = inputs.gaussian_fields(L, 4, seed=61)
+    P = [oracle_lib.heatbath(L, U, xi, m, tol=1e-12) for xi in xis]
+    noise = list(inputs.gaussian_fields(L, 8, seed=62))
+    edges = np.linspace(0.0, 1.0, 9)
+    spec, num, tr, _ = oracle_lib.power_spectrum(L, U, P, noise, 64, edges)
+    centres = 0.5 * (edges[:-1] + edges[1:])
+    mean = spec.mean(axis=0)
+    # windows that hold a good share of the modes (the spectrum of A is concentrated in the middle)
+    ok = tr > 0.05 * tr.sum()
+    target = (1 - 0.9) + 0.9 * centres
+    assert np.all(np.abs(mean[ok] / target[ok] - 1) < 0.08), (mean, target, tr)
