@@ -21,9 +21,7 @@ Carlo in lattice QCD", LATTICE2021 (arXiv:2112.04556).
   Sec. 3: implicit (generalised) leapfrog of Girolami & Calderhead.
 
 Parity pins: every function here is checked in tests/test_oracle_*.py against
-closed forms, invariants, dense linear algebra or finite differences; the one
-exception is stated in `leapfrog_step` (exact volume preservation of the
-group-valued implicit step: parity unpinned).
+closed forms, invariants, dense linear algebra or finite differences.
 """
 import ctypes
 import math
@@ -452,8 +450,9 @@ def leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol=1e-13, fp_tol=1e-13, fp_
     and keeps V(U, Q_i).  Step (2) starts from exp(i eps V(U,P')) U, evaluates V and F_K at
     (W_i, P') and stops when max|W_{i+1}-W_i| <= fp_tol, keeping F_K(W_i, P') for step (3).
     The Lie-Poisson term of the group flow is not included (it changes neither H nor the
-    phase-space volume of the continuous flow); exact volume preservation of this discrete
-    group step: parity unpinned.
+    phase-space volume of the continuous flow).  Phase-space volume: exact for a link-independent
+    mass; with a link-dependent mass the group exponentials leave log det J = O(eps^3) per step
+    (finite-difference Jacobians in tests/test_oracle_hmc.py).
     FG (optional) is F_G(U) if the caller has it.  With an auxiliary field phi, F_G stands for the whole
     potential force F_G + F_aux (both depend on U only).
     Returns (U'', P'', next initial guess, iteration counts, F_G(U''))."""

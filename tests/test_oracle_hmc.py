@@ -174,3 +174,67 @@ def test_aux_energy_error_scales_as_step_squared(oracle_lib):
         U1, P1, _ = oracle_lib.md_trajectory(L, U, P, 0.5, n, 6.0, 0.0, m, phi=phi)
         dH.append(H(U1, P1) - H0)
     assert 3.0 < dH[0] / dH[1] < 5.0, dH
+
+
+def _log_near_identity(W):
+    """-i log W for a unitary W within ~1e-4 of the identity (series of log(1 + E) to E^4)."""
+    E = W - np.eye(3)
+    E2 = H.mm(E, E)
+    return -1j * (E - E2 / 2 + H.mm(E2, E) / 3 - H.mm(E2, E2) / 4)
+
+
+def _step_log_jacobian(oracle_lib, L, U0, P0, eps, m, d=1e-5):
+    """log |det| of the Jacobian of one leapfrog step (U, P) -> (U'', P'') with respect to Haar x
+    Lebesgue measure, by central differences: links are moved as exp(i w) U and read back as
+    w'' = -i log(U''(w) U''(0)^dagger), so at w = 0 the coordinate volume is the Haar volume."""
+    def step(U, P):
+        r = oracle_lib.md_trajectory(L, U, P, eps, 1, 6.0, 0.0, m, tol=1e-14, fp_tol=1e-14, fp_maxit=200)
+        return r[0], r[1]
+
+    U1, _ = step(U0, P0)
+    U1d = H.dag(U1)
+    n = P0.size
+    J = np.empty((2 * n, 2 * n))
+    for k in range(2 * n):
+        outs = []
+        for s in (+1, -1):
+            e = np.zeros(n)
+            e[k % n] = s * d
+            e = e.reshape(P0.shape)
+            if k < n:
+                Ua, Pa = step(H.mm(oracle_lib.exp_i(e), U0), P0)
+            else:
+                Ua, Pa = step(U0, P0 + e)
+            w = H.to_coef(_log_near_identity(H.mm(Ua, U1d)))
+            outs.append(np.concatenate([w.ravel(), Pa.ravel()]))
+        J[:, k] = (outs[0] - outs[1]) / (2 * d)
+    sign, logdet = np.linalg.slogdet(J)
+    assert sign > 0
+    return logdet
+
+
+def test_leapfrog_volume_identity_mass(oracle_lib):
+    """M = 1: every sub-step is a shear (P by a force of U alone, U by a left translation
+    exp(i eps P') U), so one step preserves the phase-space volume exactly."""
+    L = (1, 1, 1, 2)
+    U = inputs.random_links(L, eps=0.5, seed=67)
+    P = inputs.gaussian_fields(L, 1, seed=68)[0]
+    assert abs(_step_log_jacobian(oracle_lib, L, U, P, 0.2, oracle_lib.identity_mass())) < 1e-8
+
+
+@pytest.mark.slow
+def test_leapfrog_volume_error_is_third_order(oracle_lib):
+    """A link-dependent mass: the generalised leapfrog of Sec. 3 written with group exponentials
+    keeps the flat-space cancellation of the sub-step Jacobians up to the non-commuting terms of
+    d exp, so log det J is not zero but, the step being symmetric (its inverse is the step with
+    -eps), it is odd in eps and starts at eps^3: halving eps divides it by ~8.  A scheme that
+    evaluated the velocity or the force at the wrong end of a sub-step would start at eps^2
+    (ratio ~4)."""
+    L = (1, 1, 1, 1)
+    U = inputs.random_links(L, eps=0.5, seed=69)
+    P = inputs.gaussian_fields(L, 1, seed=70)[0]
+    m = fit.mass_term(4, 0.5)
+    a = _step_log_jacobian(oracle_lib, L, U, P, 0.05, m)
+    b = _step_log_jacobian(oracle_lib, L, U, P, 0.025, m)
+    assert abs(b) > 1e-6, b
+    assert 6.5 < a / b < 17.0, (a, b)
