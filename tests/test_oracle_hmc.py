@@ -238,3 +238,29 @@ def test_leapfrog_volume_error_is_third_order(oracle_lib):
     b = _step_log_jacobian(oracle_lib, L, U, P, 0.025, m)
     assert abs(b) > 1e-6, b
     assert 6.5 < a / b < 17.0, (a, b)
+
+
+@pytest.mark.slow
+def test_plain_hmc_strong_coupling_plaquette(oracle_lib):
+    """The chain samples exp(-S) with the action normalised as in Sec. 2: at small beta the
+    plaquette follows the strong-coupling (character) expansion.  One plaquette with weight
+    exp(beta/3 ReTr U) under Haar measure has log Z = (beta/3)^2 <(ReTr U)^2>/2
+    + (beta/3)^3 <(ReTr U)^3>/6 + ..., with the SU(3) Haar moments <|Tr U|^2> = 1,
+    <(Tr U)^2> = 0, <(Tr U)^3> = 1 (so <(ReTr U)^2> = 1/2, <(ReTr U)^3> = 1/4), a vanishing fourth
+    cumulant (<|Tr U|^4> = 2) and a fifth cumulant of -5/16; d log Z / d beta gives
+    <ReTr U_p / 3> = beta/18 + beta^2/216 - 25 beta^4/466560 + ...  On the lattice the first
+    correction comes from closed cubes, O(u^5) ~ 1e-6 at beta = 1.  100 trajectories on 4^4 resolve
+    the beta^2 term at several standard deviations."""
+    L = (4, 4, 4, 4)
+    beta = 1.0
+    U = inputs.random_links(L, eps=1.0, seed=3)
+    U, _ = oracle_lib.plain_hmc(L, U, 5, beta, seed=11)
+    plaq = []
+    for n in range(100):
+        U, _ = oracle_lib.plain_hmc(L, U, 1, beta, seed=1000 + n)
+        plaq.append(oracle_lib.action(L, U, beta)[1])
+    plaq = np.array(plaq)
+    err = plaq.std() / math.sqrt(len(plaq))
+    u = beta / 18 + beta ** 2 / 216 - 25 * beta ** 4 / 466560
+    assert abs(plaq.mean() - u) < 4 * err, (plaq.mean(), u, err)
+    assert plaq.mean() - beta / 18 > 0.5 * beta ** 2 / 216, (plaq.mean(), err)
