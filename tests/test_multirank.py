@@ -51,3 +51,26 @@ def test_reference_arm_other_ranks_do_nothing(capsys):
     args = argparse.Namespace(steps=1, warmup=0)
     assert bench.run_reference(args, rank=1, world=2) == 0
     assert capsys.readouterr().out == ""
+
+
+@pytest.mark.slow
+def test_reference_arm_json_line(capsys):
+    """Rank 0 of `bench.py --impl reference` times the oracle on its bounded sample and prints one JSON
+    line with the benchmark's metric, unit and direction, a cpu_baseline of kind "oracle" and an e2e
+    object that moves no bytes between host and device."""
+    import argparse
+    import json
+
+    import bench
+    args = argparse.Namespace(steps=1, warmup=0, nsteps=bench.NSTEPS)
+    assert bench.run_reference(args, rank=0, world=1) == 0
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "traj/s"
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1
+    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 / d["value"]) < 1e-6 * d["ms_per_step"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "traj/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("32^4 full RMHMC")
