@@ -486,21 +486,125 @@ def leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol=1e-13, fp_tol=1e-13, fp_
     return W, P2, Qnext, (i1, i2), FG1
 
 
-def md_trajectory(L, U, P, tau, nsteps, beta, c1, mass, tol=1e-13, fp_tol=1e-13, fp_maxit=100, phi=None):
+# --------------------------------------------------------------------------
+# Sec. 3's implicit leapfrog written as a Lie-group variational integrator (exactly symplectic on
+# T*SU(3)).  The generalised leapfrog is the composition of the two symplectic Euler methods; on the
+# group, symplectic Euler comes from the discrete Lagrangian h L(U, xi) with exp(i h xi) = U_{k+1} U_k^-1,
+# whose discrete Legendre transforms carry the right-trivialised derivative of the exponential.
+# --------------------------------------------------------------------------
+
+def ad(X, Y):
+    """ad_X Y: coefficients of i [X^a T^a, Y^b T^b] (the bracket of the generators i X.T and i Y.T)."""
+    A = coef_to_mat(X)
+    B = coef_to_mat(Y)
+    return mat_to_coef(1j * (np.matmul(A, B) - np.matmul(B, A)))
+
+
+def ad_matrix(X):
+    """8x8 matrix (per link) of Y -> ad_X Y."""
+    X = _c(X, np.float64)
+    cols = []
+    for b in range(8):
+        e = np.zeros(X.shape)
+        e[..., b] = 1.0
+        cols.append(ad(X, e))
+    return np.stack(cols, axis=-1)
+
+
+def dexp_matrix(X, nterms=40):
+    """8x8 matrix (per link) of dexp_X = sum_n ad_X^n / (n+1)!, the right-trivialised derivative of the
+    exponential: d/dt exp(i (X + t Y).T) exp(-i X.T) = i (dexp_X Y).T.  The series is entire."""
+    A = ad_matrix(X)
+    term = np.broadcast_to(np.eye(8), A.shape).copy()
+    acc = term.copy()
+    fact = 1.0
+    for n in range(1, nterms):
+        term = np.matmul(A, term)
+        fact *= n + 1
+        acc = acc + term / fact
+    return acc
+
+
+def dexp(X, Y):
+    return np.einsum("...ab,...b->...a", dexp_matrix(X), Y)
+
+
+def dexp_inv(X, Y):
+    """Z with dexp_X Z = Y, by a linear solve per link."""
+    return np.linalg.solve(dexp_matrix(X), _c(Y, np.float64)[..., None])[..., 0]
+
+
+def symplectic_step(L, U, P, eps, beta, c1, mass, Q0, tol=1e-13, fp_tol=1e-13, fp_maxit=100, FG=None, phi=None):
+    """One step of the implicit leapfrog as the composition of the two Lie-group symplectic Euler maps
+    of half a step, h = eps/2 (F = F_G + F_K, V = M^{-1} P as in `leapfrog_step`):
+      (A) mu:  dexp^{-1}_{X1} mu = P + h F(U, mu),  X1 = h V(U, mu);  B = exp(i X1) U;
+          P_h = dexp^{-1}_{-X1} mu
+      (B) (mu2, U'):  dexp^{-1}_{X2} mu2 = P_h,  X2 = h V(U', mu2),  U' = exp(i X2) B;
+          P'' = dexp^{-1}_{-X2} mu2 + h F(U', mu2).
+    Each half is the discrete Legendre transform of the discrete Lagrangian h L(U_k, xi) (A) or
+    h L(U_{k+1}, xi) (B) with L = 1/2 xi.M xi - S; each is symplectic and B is the adjoint of A, so the
+    step preserves the phase-space volume exactly and is reversible.  With dexp = 1 it is
+    `leapfrog_step`; to first order in h the dexp terms add the Lie-Poisson term ad_V P to dP/dt.
+    Iteration rules as in `leapfrog_step`: (A) starts from Q0 and, at iterate mu_i, evaluates F_K and V
+    at (U, mu_i), sets mu_{i+1} = dexp_{h V}(P + h F) and stops when max|mu_{i+1} - mu_i| <= fp_tol,
+    keeping X1 = h V(U, mu_i).  (B) starts from mu2 = mu_{i+1} and W = exp(2 i X1) U; at (W_j, mu2_j) it
+    evaluates F_K and V, sets X2 = h V, mu2_{j+1} = dexp_{X2} P_h, W_{j+1} = exp(i X2) B, and stops when
+    the larger of max|W_{j+1} - W_j| and max|mu2_{j+1} - mu2_j| is <= fp_tol, keeping F_K and X2 of
+    (W_j, mu2_j).
+    Returns (U'', P'', next initial guess, iteration counts, F_G(U''))."""
+    h = 0.5 * eps
+    if FG is None:
+        FG = potential_force(L, U, beta, c1, mass, phi, tol)
+    mu = Q0
+    for i1 in range(1, fp_maxit + 1):
+        _, FK, V = kinetic(L, U, mu, mass, tol)
+        mun = dexp(h * V, P + h * (FG + FK))
+        done = _maxabs(mun - mu) <= fp_tol
+        mu = mun
+        if done:
+            break
+    else:
+        raise RuntimeError("oracle: momentum fixed point did not converge")
+    X1 = h * V
+    B = np.matmul(exp_i(X1), U)
+    Ph = dexp_inv(-X1, mu)
+    mu2 = mu
+    W = np.matmul(exp_i(2.0 * X1), U)
+    for i2 in range(1, fp_maxit + 1):
+        _, FK1, V1 = kinetic(L, W, mu2, mass, tol)
+        X2 = h * V1
+        mu2n = dexp(X2, Ph)
+        Wn = np.matmul(exp_i(X2), B)
+        done = max(_maxabs(Wn - W), _maxabs(mu2n - mu2)) <= fp_tol
+        W, mu2 = Wn, mu2n
+        if done:
+            break
+    else:
+        raise RuntimeError("oracle: link fixed point did not converge")
+    FG1 = potential_force(L, W, beta, c1, mass, phi, tol)
+    P2 = dexp_inv(-X2, mu2) + h * (FG1 + FK1)
+    Qnext = P2 + h * (FG1 + FK1)
+    return W, P2, Qnext, (i1, i2), FG1
+
+
+def md_trajectory(L, U, P, tau, nsteps, beta, c1, mass, tol=1e-13, fp_tol=1e-13, fp_maxit=100, phi=None,
+                  symplectic=False):
     """nsteps generalised-leapfrog steps of size tau/nsteps; the first momentum
-    fixed point starts from P + eps/2 F_G(U) (F_G + F_aux with an auxiliary field phi)."""
+    fixed point starts from P + eps/2 F_G(U) (F_G + F_aux with an auxiliary field phi).
+    symplectic=True takes `symplectic_step` instead of `leapfrog_step`."""
     eps = tau / nsteps
     FG = potential_force(L, U, beta, c1, mass, phi, tol)
     Q0 = P + 0.5 * eps * FG
     iters = []
+    step = symplectic_step if symplectic else leapfrog_step
     for _ in range(nsteps):
-        U, P, Q0, it, FG = leapfrog_step(L, U, P, eps, beta, c1, mass, Q0, tol, fp_tol, fp_maxit, FG, phi)
+        U, P, Q0, it, FG = step(L, U, P, eps, beta, c1, mass, Q0, tol, fp_tol, fp_maxit, FG, phi)
         iters.append(it)
     return U, P, iters
 
 
 def trajectory(L, U, xi, u, tau, nsteps, beta, c1, mass, tol_md=1e-13, tol_h=1e-13,
-               fp_tol=1e-13, fp_maxit=100, metropolis=True, eta=None):
+               fp_tol=1e-13, fp_maxit=100, metropolis=True, eta=None, symplectic=False):
     """One RMHMC trajectory: heatbath P = M^{1/2} xi, H0, MD, H1, accept if u <= exp(-dH).
     With eta (a Gaussian field), the log|M| term is included through the auxiliary field
     phi = R(A) eta, held fixed in the MD, and H = T + S + S_aux."""
@@ -508,7 +612,7 @@ def trajectory(L, U, xi, u, tau, nsteps, beta, c1, mass, tol_md=1e-13, tol_h=1e-
     P0 = heatbath(L, U, xi, mass, tol_h)
     H0, T0, S0, _ = hamiltonian(L, U, P0, beta, c1, mass, tol_h)
     A0 = aux_action(L, U, phi, mass, tol_h) if phi is not None else 0.0
-    U1, P1, iters = md_trajectory(L, U, P0, tau, nsteps, beta, c1, mass, tol_md, fp_tol, fp_maxit, phi)
+    U1, P1, iters = md_trajectory(L, U, P0, tau, nsteps, beta, c1, mass, tol_md, fp_tol, fp_maxit, phi, symplectic)
     H1, T1, S1, plaq1 = hamiltonian(L, U1, P1, beta, c1, mass, tol_h)
     A1 = aux_action(L, U1, phi, mass, tol_h) if phi is not None else 0.0
     H0 += A0

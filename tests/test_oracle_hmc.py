@@ -183,15 +183,16 @@ def _log_near_identity(W):
     return -1j * (E - E2 / 2 + H.mm(E2, E) / 3 - H.mm(E2, E2) / 4)
 
 
-def _step_log_jacobian(oracle_lib, L, U0, P0, eps, m, d=1e-5):
-    """log |det| of the Jacobian of one leapfrog step (U, P) -> (U'', P'') with respect to Haar x
-    Lebesgue measure, by central differences: links are moved as exp(i w) U and read back as
-    w'' = -i log(U''(w) U''(0)^dagger), so at w = 0 the coordinate volume is the Haar volume."""
+def _step_jacobian(oracle_lib, L, U0, P0, eps, m, symplectic=False, d=1e-5):
+    """Jacobian of one step (U, P) -> (U'', P'') in right-trivialised coordinates, by central
+    differences: links are moved as exp(i w) U and read back as w'' = -i log(U''(w) U''(0)^dagger), so
+    at w = 0 the coordinate volume is the Haar volume.  Returns (J, P'')."""
     def step(U, P):
-        r = oracle_lib.md_trajectory(L, U, P, eps, 1, 6.0, 0.0, m, tol=1e-14, fp_tol=1e-14, fp_maxit=200)
+        r = oracle_lib.md_trajectory(L, U, P, eps, 1, 6.0, 0.0, m, tol=1e-14, fp_tol=1e-14, fp_maxit=200,
+                                     symplectic=symplectic)
         return r[0], r[1]
 
-    U1, _ = step(U0, P0)
+    U1, P1 = step(U0, P0)
     U1d = H.dag(U1)
     n = P0.size
     J = np.empty((2 * n, 2 * n))
@@ -208,7 +209,12 @@ def _step_log_jacobian(oracle_lib, L, U0, P0, eps, m, d=1e-5):
             w = H.to_coef(_log_near_identity(H.mm(Ua, U1d)))
             outs.append(np.concatenate([w.ravel(), Pa.ravel()]))
         J[:, k] = (outs[0] - outs[1]) / (2 * d)
-    sign, logdet = np.linalg.slogdet(J)
+    return J, P1
+
+
+def _step_log_jacobian(oracle_lib, L, U0, P0, eps, m, symplectic=False):
+    """log |det| of the step's Jacobian with respect to Haar x Lebesgue measure."""
+    sign, logdet = np.linalg.slogdet(_step_jacobian(oracle_lib, L, U0, P0, eps, m, symplectic)[0])
     assert sign > 0
     return logdet
 
@@ -264,3 +270,95 @@ def test_plain_hmc_strong_coupling_plaquette(oracle_lib):
     u = beta / 18 + beta ** 2 / 216 - 25 * beta ** 4 / 466560
     assert abs(plaq.mean() - u) < 4 * err, (plaq.mean(), u, err)
     assert plaq.mean() - beta / 18 > 0.5 * beta ** 2 / 216, (plaq.mean(), err)
+
+
+def _structure_constants():
+    """f^{abc} of su(3) from [T^a, T^b] = i f^{abc} T^c with the Gell-Mann matrices of the helpers."""
+    T = H.TGEN
+    f = np.empty((8, 8, 8))
+    for a in range(8):
+        for b in range(8):
+            C = H.mm(T[a], T[b]) - H.mm(T[b], T[a])
+            for c in range(8):
+                f[a, b, c] = np.real(-2j * np.trace(H.mm(C, T[c])))
+    return f
+
+
+def _canonical_form(P):
+    """Matrix of the canonical symplectic form of T*SU(3)^links at momenta P in right-trivialised
+    coordinates (w, P): with the Liouville form theta = P.w and right-invariant fields, whose bracket is
+    [X_a, X_b] = f^{abc} X_c, d theta((w1, P1), (w2, P2)) = P1.w2 - P2.w1 - f^{abc} w1^a w2^b P^c."""
+    f = _structure_constants()
+    Pl = P.reshape(-1, 8)
+    n = Pl.size
+    K = np.zeros((n, n))
+    for l in range(len(Pl)):
+        K[8 * l:8 * l + 8, 8 * l:8 * l + 8] = -np.einsum("abc,c->ab", f, Pl[l])
+    return np.block([[K, -np.eye(n)], [np.eye(n), np.zeros((n, n))]])
+
+
+def test_dexp_against_finite_differences(oracle_lib):
+    """dexp_X Y = -i log(exp(i(X + tY).T) exp(-iX.T)) / t as t -> 0 (scipy's expm and logm), and
+    dexp_inv inverts it; for Y parallel to X, dexp_X Y = Y."""
+    import scipy.linalg as sl
+    rng = np.random.default_rng(71)
+    X = rng.standard_normal((3, 8)) * np.array([[0.1], [0.7], [2.0]])
+    Y = rng.standard_normal((3, 8))
+    D = oracle_lib.dexp(X, Y)
+    t = 1e-6
+    for l in range(3):
+        Ep = sl.expm(1j * H.to_mat(X[l] + t * Y[l]))
+        Em = sl.expm(1j * H.to_mat(X[l] - t * Y[l]))
+        E0 = sl.expm(-1j * H.to_mat(X[l]))
+        fd = H.to_coef(-1j * (sl.logm(Ep @ E0) - sl.logm(Em @ E0))) / (2 * t)
+        assert np.abs(fd - D[l]).max() < 1e-8 * max(1.0, np.abs(D[l]).max())
+    assert np.abs(oracle_lib.dexp_inv(X, D) - Y).max() < 1e-12
+    assert np.abs(oracle_lib.dexp(X, 0.3 * X) - 0.3 * X).max() < 1e-14
+
+
+@pytest.mark.slow
+def test_symplectic_step_preserves_the_canonical_form(oracle_lib):
+    """The Lie-group variational form of the implicit leapfrog is a symplectic map of T*SU(3):
+    J^T Omega(P'') J = Omega(P) for the canonical form, so det J = 1; the form with the opposite sign
+    of its structure-constant term is not preserved (the check sees that term), and the plain
+    group-exponential leapfrog preserves neither."""
+    L = (1, 1, 1, 1)
+    U = inputs.random_links(L, eps=0.5, seed=69)
+    P = inputs.gaussian_fields(L, 1, seed=70)[0]
+    m = fit.mass_term(4, 0.5)
+    J, P1 = _step_jacobian(oracle_lib, L, U, P, 0.1, m, symplectic=True)
+    assert np.abs(J.T @ _canonical_form(P1) @ J - _canonical_form(P)).max() < 1e-8
+    assert abs(np.linalg.slogdet(J)[1]) < 1e-8
+    assert np.abs(J.T @ _canonical_form(-P1) @ J - _canonical_form(-P)).max() > 1e-2
+    J0, P10 = _step_jacobian(oracle_lib, L, U, P, 0.1, m, symplectic=False)
+    assert np.abs(J0.T @ _canonical_form(P10) @ J0 - _canonical_form(P)).max() > 1e-3
+
+
+def test_symplectic_step_reversible_and_plain_for_identity_mass(oracle_lib):
+    """Forward, momentum flip, forward returns to the start; with M = 1 (V = P, ad_P P = 0) the dexp
+    factors drop out and the step is the group-exponential leapfrog."""
+    L = L2
+    U = inputs.random_links(L, eps=0.3, seed=72)
+    P = inputs.gaussian_fields(L, 1, seed=73)[0]
+    m = fit.mass_term(8, 0.9)
+    U1, P1, _ = oracle_lib.md_trajectory(L, U, P, 0.2, 2, 6.0, 0.0, m, tol=1e-14, symplectic=True)
+    U2, P2, _ = oracle_lib.md_trajectory(L, U1, -P1, 0.2, 2, 6.0, 0.0, m, tol=1e-14, symplectic=True)
+    assert np.abs(U2 - U).max() < 1e-11 and np.abs(P2 + P).max() < 1e-10
+    I = oracle_lib.identity_mass()
+    Ua, Pa, _ = oracle_lib.md_trajectory(L, U, P, 0.3, 3, 6.0, -0.331, I, symplectic=True)
+    Ub, Pb, _ = oracle_lib.md_trajectory(L, U, P, 0.3, 3, 6.0, -0.331, I, symplectic=False)
+    assert np.abs(Ua - Ub).max() < 1e-12 and np.abs(Pa - Pb).max() < 1e-11
+
+
+@pytest.mark.slow
+def test_symplectic_energy_error_scales_as_step_squared(oracle_lib):
+    L = L2
+    U = inputs.random_links(L, eps=0.3, seed=63)
+    P = inputs.gaussian_fields(L, 1, seed=64)[0]
+    m = fit.mass_term(8, 0.9)
+    H0 = oracle_lib.hamiltonian(L, U, P, 6.0, 0.0, m)[0]
+    dH = []
+    for n in (5, 10):
+        U1, P1, _ = oracle_lib.md_trajectory(L, U, P, 0.5, n, 6.0, 0.0, m, symplectic=True)
+        dH.append(oracle_lib.hamiltonian(L, U1, P1, 6.0, 0.0, m)[0] - H0)
+    assert 3.0 < dH[0] / dH[1] < 5.0, dH
