@@ -110,6 +110,17 @@ typedef struct {
     int logdet;         /* 1: the log|M| term of Eq. (5) through an auxiliary field phi = R(A) eta (eta from
                            Philox(seed, traj_index, tag 3)), held fixed in the MD, with action
                            1/2 <phi, M phi> = 1/2 |R(A)^{-1} phi|^2 in H and its force in the MD (needs c > 0) */
+    int symplectic;     /* 0: the implicit leapfrog of Sec. 3 with group exponentials (momentum half steps
+                           P' = P + eps/2 F(U, P'), links U' = exp(i eps/2 V(U',P')) exp(i eps/2 V(U,P')) U);
+                           1: its exactly symplectic form on T*SU(3), the same steps with the momenta passed
+                           through the right-trivialised derivative of the exponential, per link
+                           dexp_X = sum_n ad_X^n/(n+1)!, X = eps/2 V:
+                             dexp^{-1}_{X1} mu = P + eps/2 F(U, mu), X1 = eps/2 V(U, mu); B = exp(i X1) U;
+                             P_h = dexp^{-1}_{-X1} mu;  dexp^{-1}_{X2} mu2 = P_h, X2 = eps/2 V(U', mu2),
+                             U' = exp(i X2) B;  P'' = dexp^{-1}_{-X2} mu2 + eps/2 F(U', mu2).
+                           It preserves phase-space volume exactly (the first form only to O(eps^3) per step
+                           with a link-dependent mass).  Host-driven MD only (no graph); dexp series in float64
+                           (float32 corrections on the mixed path).  Any other value: RMHMC_EINVAL. */
 } rmhmc_params;
 
 typedef struct {

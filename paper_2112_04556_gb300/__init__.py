@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
                 ("nsteps", ctypes.c_int), ("tol_md", ctypes.c_double), ("tol_h", ctypes.c_double),
                 ("fp_tol", ctypes.c_double), ("fp_maxit", ctypes.c_int), ("maxiter", ctypes.c_int),
                 ("prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("traj_index", ctypes.c_uint32),
-                ("metropolis", ctypes.c_int), ("logdet", ctypes.c_int)]
+                ("metropolis", ctypes.c_int), ("logdet", ctypes.c_int), ("symplectic", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -420,12 +420,13 @@ def wilson_flow(ctx, U, eps, nsteps, prec=FP64, stream=None):
 
 
 def make_params(beta=6.0, c1=0.0, mass=None, tau=1.0, nsteps=20, tol_md=1e-10, tol_h=1e-11, fp_tol=1e-10,
-                fp_maxit=50, maxiter=2000, prec=FP64, seed=0, traj_index=0, metropolis=True, logdet=False):
+                fp_maxit=50, maxiter=2000, prec=FP64, seed=0, traj_index=0, metropolis=True, logdet=False,
+                symplectic=False):
     mass = mass if mass is not None else {"c": 1.0, "alpha": [], "sigma": [], "kappa": 0.0}
     ms = _mass_struct(mass)
     p = Params(float(beta), float(c1), ms, float(tau), int(nsteps), float(tol_md), float(tol_h),
                float(fp_tol), int(fp_maxit), int(maxiter), int(prec), int(seed), int(traj_index), int(bool(metropolis)),
-               int(bool(logdet)))
+               int(bool(logdet)), int(bool(symplectic)))
     p._keep = ms._keep   # the struct copy holds raw pointers into these arrays
     return p
 

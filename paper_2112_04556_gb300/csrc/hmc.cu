@@ -296,6 +296,145 @@ __global__ void k_mom_update(const double* __restrict__ P, double h, const doubl
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Exactly symplectic form of the step (rmhmc_params.symplectic): the momenta pass through the
+// right-trivialised derivative of the exponential, dexp_X = sum_n ad_X^n / (n+1)!, per link, with
+// ad_X Y = coefficients of i[X.T, Y.T] = -f_abc X_a Y_b e_c (f the totally antisymmetric su(3)
+// structure constants).  The identity term is added in float64; the series terms are summed in TC
+// (float64 on the float64 path, float32 on the mixed one, where they are a correction of relative
+// size |X| to momenta whose forces are float32 already).
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void ad_su3(const T (&X)[8], const T (&Y)[8], T (&Z)[8]) {
+    constexpr int tr[9][3] = {{0, 1, 2}, {0, 3, 6}, {0, 4, 5}, {1, 3, 5}, {1, 4, 6},
+                              {2, 3, 4}, {2, 5, 6}, {3, 4, 7}, {5, 6, 7}};
+    constexpr double fv[9] = {1.0, 0.5, -0.5, 0.5, 0.5, 0.5, -0.5, 0.86602540378443864676, 0.86602540378443864676};
+#pragma unroll
+    for (int c = 0; c < 8; c++) Z[c] = T(0);
+#pragma unroll
+    for (int t = 0; t < 9; t++) {
+        const int i = tr[t][0], j = tr[t][1], k = tr[t][2];
+        const T v = (T)fv[t];
+        Z[k] -= v * (X[i] * Y[j] - X[j] * Y[i]);
+        Z[i] -= v * (X[j] * Y[k] - X[k] * Y[j]);
+        Z[j] -= v * (X[k] * Y[i] - X[i] * Y[k]);
+    }
+}
+
+// S = sum_{n>=1} ad_X^n Y / (n+1)!  (dexp_X Y = Y + S); the terms fall at least as |X|^n/(n+1)!
+template <typename T>
+__device__ __forceinline__ void dexp_tail(const T (&X)[8], const T (&Y)[8], T (&S)[8]) {
+    T t[8], u[8];
+    T ymax = T(0);
+#pragma unroll
+    for (int a = 0; a < 8; a++) { t[a] = Y[a]; S[a] = T(0); ymax = fmax(ymax, fabs(Y[a])); }
+    const T stop = ymax * (sizeof(T) == 8 ? T(1e-18) : T(1e-9));
+    for (int n = 1; n <= 40; n++) {
+        ad_su3(X, t, u);
+        T mx = T(0);
+#pragma unroll
+        for (int a = 0; a < 8; a++) { t[a] = u[a] / T(n + 1); S[a] += t[a]; mx = fmax(mx, fabs(t[a])); }
+        if (mx <= stop) break;
+    }
+}
+
+// S = sum_{n>=1} (B_n / n!) ad_X^n Y, Bernoulli numbers B_n (z/(e^z - 1) = sum B_n z^n / n!), to n = 16:
+// dexp^{-1}_X Y = Y + S up to (|ad_X|/2 pi)^18
+__constant__ double kBernoulliOverFactorial[17] = {
+    1.0, -0.5, 1.0 / 12.0, 0.0, -1.0 / 720.0, 0.0, 1.0 / 30240.0, 0.0, -1.0 / 1209600.0, 0.0, 1.0 / 47900160.0, 0.0,
+    -691.0 / 1307674368000.0, 0.0, 1.0 / 74724249600.0, 0.0, -3617.0 / 10670622842880000.0};
+
+template <typename T>
+__device__ __forceinline__ void dexpinv_tail(const T (&X)[8], const T (&Y)[8], T (&S)[8]) {
+    const double* bn = kBernoulliOverFactorial;
+    T w[8], u[8];
+#pragma unroll
+    for (int a = 0; a < 8; a++) { w[a] = Y[a]; S[a] = T(0); }
+#pragma unroll 1
+    for (int n = 1; n <= 16; n++) {
+        ad_su3(X, w, u);
+#pragma unroll
+        for (int a = 0; a < 8; a++) { w[a] = u[a]; S[a] += T(bn[n]) * w[a]; }
+    }
+}
+
+// Per link (thread per link of [V][4][8] coefficient fields), X = h V:
+//   inverse = 0:  out = dexp_X (Y + h (F1 + F2))
+//   inverse = 1:  out = dexp^{-1}_{-X} Y + h (F1 + F2)   (Bernoulli series plus residual corrections)
+// F1, F2 may be null.  With Qold, max |out - Qold| goes to *maxdiff; |X| > 4 (the step turns a link
+// by more than 4 radians: the Bernoulli series needs |ad_X| < 2 pi) writes NaN and reports divergence.
+template <typename TC>
+__global__ void __launch_bounds__(kBlock) k_mom_dexp(int inverse, const double* __restrict__ Y, double h,
+                                                     const double* __restrict__ F1, const double* __restrict__ F2,
+                                                     const double* __restrict__ V, const double* Qold, double* out,
+                                                     size_t nlink, double* maxdiff) {
+    double diff = 0.0;
+    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < nlink; l += (size_t)gridDim.x * blockDim.x) {
+        const size_t o = l * 8;
+        double y[8], f[8], r[8];
+        TC x[8], yc[8], s[8];
+        double xx = 0.0;
+#pragma unroll
+        for (int a = 0; a < 8; a++) {
+            const double xa = (inverse ? -h : h) * V[o + a];
+            xx += xa * xa;
+            x[a] = (TC)xa;
+            f[a] = h * ((F1 ? F1[o + a] : 0.0) + (F2 ? F2[o + a] : 0.0));
+            y[a] = inverse ? Y[o + a] : Y[o + a] + f[a];
+            yc[a] = (TC)y[a];
+        }
+        if (!inverse) {
+            dexp_tail(x, yc, s);
+#pragma unroll
+            for (int a = 0; a < 8; a++) r[a] = y[a] + (double)s[a];
+        } else {
+            // z = y + d with d = B(y) - y (B the truncated Bernoulli series), then refinements
+            // d += B(y - dexp(z)), y - dexp(z) = -(d + dexp_tail(z)), each gaining (|ad_X| / 2 pi)^17
+            TC d[8], z[8], t[8], rr[8], b[8];
+            dexpinv_tail(x, yc, d);
+            TC ymax = TC(0);
+#pragma unroll
+            for (int a = 0; a < 8; a++) ymax = fmax(ymax, fabs(yc[a]));
+            const TC stop = ymax * (sizeof(TC) == 8 ? TC(1e-17) : TC(1e-8));
+#pragma unroll 1
+            for (int it = 0; it < 8; it++) {
+#pragma unroll
+                for (int a = 0; a < 8; a++) z[a] = yc[a] + d[a];
+                dexp_tail(x, z, t);
+#pragma unroll
+                for (int a = 0; a < 8; a++) rr[a] = -(d[a] + t[a]);
+                dexpinv_tail(x, rr, b);
+                TC mx = TC(0);
+#pragma unroll
+                for (int a = 0; a < 8; a++) { const TC c = rr[a] + b[a]; d[a] += c; mx = fmax(mx, fabs(c)); }
+                if (mx <= stop) break;
+            }
+#pragma unroll
+            for (int a = 0; a < 8; a++) r[a] = y[a] + (double)d[a] + f[a];
+        }
+        const bool bad = xx > 16.0;
+#pragma unroll
+        for (int a = 0; a < 8; a++) {
+            if (bad) r[a] = __longlong_as_double(0x7ff8000000000000LL);
+            if (Qold) diff = fmax(diff, bad ? INFINITY : fabs(r[a] - Qold[o + a]));
+        }
+#pragma unroll
+        for (int a = 0; a < 8; a++) out[o + a] = r[a];
+    }
+    if (maxdiff) {
+        __shared__ double sh[kBlock / 32];
+#pragma unroll
+        for (int w = 16; w > 0; w >>= 1) diff = fmax(diff, __shfl_down_sync(0xffffffffu, diff, w));
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = diff;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = 0.0;
+            for (int w = 0; w < kBlock / 32; w++) m = fmax(m, sh[w]);
+            atomic_max_nonneg(maxdiff, m);
+        }
+    }
+}
+
 __global__ void k_gauss_field(double* __restrict__ out, int V, uint64_t seed, uint32_t stream, uint32_t tag) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= V) return;
@@ -352,8 +491,22 @@ static int mom_update(rmhmc_ctx* ctx, const double* P, double h, const double* F
     return RMHMC_OK;
 }
 
+static int mom_dexp(rmhmc_ctx* ctx, int prec, bool inverse, const double* Y, double h, const double* F1,
+                    const double* F2, const double* V, const double* Qold, double* out, double* dmax, cudaStream_t st) {
+    const size_t nl = (size_t)ctx->g.V * 4;
+    const int grid = (int)std::min<size_t>((nl + kBlock - 1) / kBlock, (size_t)ctx->num_sms * 8);
+    if (prec == RMHMC_FP64)
+        k_mom_dexp<double><<<grid, kBlock, 0, st>>>(inverse ? 1 : 0, Y, h, F1, F2, V, Qold, out, nl, dmax);
+    else
+        k_mom_dexp<float><<<grid, kBlock, 0, st>>>(inverse ? 1 : 0, Y, h, F1, F2, V, Qold, out, nl, dmax);
+    ++ctx->launches;
+    RM_LAUNCH_CHECK(ctx);
+    return RMHMC_OK;
+}
+
 struct MDWork {
     double *FG, *FK, *V0, *Q, *B, *W, *dmax;
+    double* Ph;   // the symplectic step's momenta after its first half (dexp^{-1}_{-X1} mu)
     float* W32;   // float32 iterate of the link fixed point (mixed precision)
 };
 
@@ -368,7 +521,8 @@ static int md_work(rmhmc_ctx* ctx, MDWork& w) {
     w.W = (double*)workspace(ctx, "md_w", sizeof(double) * ls, &status);
     w.dmax = (double*)workspace(ctx, "md_dmax", 64, &status);
     w.W32 = (float*)workspace(ctx, "md_w32", sizeof(float) * (size_t)ctx->g.V * 72, &status);
-    if (!w.FG || !w.FK || !w.V0 || !w.Q || !w.B || !w.W || !w.dmax || !w.W32) return status;
+    w.Ph = (double*)workspace(ctx, "md_ph", sizeof(double) * fs, &status);
+    if (!w.FG || !w.FK || !w.V0 || !w.Q || !w.B || !w.W || !w.dmax || !w.W32 || !w.Ph) return status;
     return RMHMC_OK;
 }
 
@@ -383,6 +537,7 @@ static int check_params(rmhmc_ctx* ctx, const rmhmc_params* p) {
     if (!(p->tol_md > 0.0) || !(p->tol_h > 0.0) || !(p->fp_tol > 0.0) || p->fp_maxit < 1 || p->maxiter < 1)
         return set_err(ctx, RMHMC_EINVAL, "tolerances and iteration caps must be positive");
     if (p->prec != RMHMC_FP64 && p->prec != RMHMC_MIXED) return set_err(ctx, RMHMC_EINVAL, "bad prec");
+    if (p->symplectic != 0 && p->symplectic != 1) return set_err(ctx, RMHMC_EINVAL, "symplectic must be 0 or 1");
     return RMHMC_OK;
 }
 
@@ -429,7 +584,8 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
             solves++;
             kiters += it;
             RM_CHECK(ctx, cudaMemsetAsync(w.dmax, 0, sizeof(double), st));
-            RM_TRY(mom_update(ctx, P, 0.5 * eps, w.FG, w.FK, w.Q, w.Q, w.dmax, st));
+            if (p->symplectic) RM_TRY(mom_dexp(ctx, p->prec, false, P, 0.5 * eps, w.FG, w.FK, w.V0, w.Q, w.Q, w.dmax, st));
+            else RM_TRY(mom_update(ctx, P, 0.5 * eps, w.FG, w.FK, w.Q, w.Q, w.dmax, st));
             double d = 0.0;
             RM_TRY(read_max(ctx, w.dmax, &d, st));
             fp_p++;
@@ -442,6 +598,8 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
         // float32 Krylov runs and the convergence test) in float32; the accepted one,
         // exp(i eps/2 V(W_i)) B, in float64.
         const bool it32 = link_iterates_fp32(p);
+        // symplectic: P_h = dexp^{-1}_{-X1} mu (X1 = eps/2 V0); the link loop then also iterates mu2 = dexp_{X2} P_h
+        if (p->symplectic) RM_TRY(mom_dexp(ctx, p->prec, true, w.Q, 0.5 * eps, nullptr, nullptr, w.V0, nullptr, w.Ph, nullptr, st));
         RM_TRY(link_update_launch(ctx, U, w.V0, 0.5 * eps, false, w.B, nullptr, nullptr, false, st));
         if (it32) RM_TRY(link_iter32_launch(ctx, U, w.V0, eps, w.W32, false, nullptr, st));
         else RM_TRY(link_update_launch(ctx, U, w.V0, eps, false, w.W, nullptr, nullptr, true, st));
@@ -455,6 +613,7 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
             // W_{i+1} (float64: into U's buffer, U is no longer needed as B holds exp(i eps/2 V0) U)
             if (it32) RM_TRY(link_iter32_launch(ctx, w.B, w.V0, 0.5 * eps, w.W32, true, w.dmax, st));
             else RM_TRY(link_update_launch(ctx, w.B, w.V0, 0.5 * eps, false, U, w.W, w.dmax, true, st));
+            if (p->symplectic) RM_TRY(mom_dexp(ctx, p->prec, false, w.Ph, 0.5 * eps, nullptr, nullptr, w.V0, w.Q, w.Q, w.dmax, st));
             double d = 0.0;
             RM_TRY(read_max(ctx, w.dmax, &d, st));
             fp_u++;
@@ -468,7 +627,8 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
         else RM_TRY(link_update_launch(ctx, w.W, w.V0, 0.0, true, U, nullptr, nullptr, true, st));
         // (3) explicit half step with F_K(W_i, P') kept from the last iteration
         RM_TRY(potential_force(ctx, p, gprec, lg, w.FG, st));
-        RM_TRY(mom_update(ctx, w.Q, 0.5 * eps, w.FG, w.FK, nullptr, P, nullptr, st));
+        if (p->symplectic) RM_TRY(mom_dexp(ctx, p->prec, true, w.Q, 0.5 * eps, w.FG, w.FK, w.V0, nullptr, P, nullptr, st));
+        else RM_TRY(mom_update(ctx, w.Q, 0.5 * eps, w.FG, w.FK, nullptr, P, nullptr, st));
         RM_TRY(mom_update(ctx, P, 0.5 * eps, w.FG, w.FK, nullptr, w.Q, nullptr, st));   // next initial guess
     }
     if (r) {
@@ -636,7 +796,8 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
 static int md_graph_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, const MassTerm& m, rmhmc_result* r,
                         cudaStream_t stream, bool* used, const AuxTerm* lg = nullptr) {
     *used = false;
-    if (!ctx->use_graphs || p->prec == RMHMC_FP64 || m.npole() == 0 || 2 * m.npole() + 1 > 32) return RMHMC_OK;
+    if (!ctx->use_graphs || p->prec == RMHMC_FP64 || p->symplectic || m.npole() == 0 || 2 * m.npole() + 1 > 32)
+        return RMHMC_OK;
     MDWork w;
     RM_TRY(md_work(ctx, w));
     MDGraphBufs gb;

@@ -200,3 +200,50 @@ def test_logdet_mixed_graph_and_host_agree_with_fp64():
     assert abs(out["graph"]["dH"] - out["host"]["dH"]) <= 1e-6
     assert abs(out["graph"]["dH"] - out["fp64"]["dH"]) <= 1e-3
     assert abs(out["fp64"]["A0"] - out["graph"]["A0"]) <= 1e-9 * out["fp64"]["A0"]
+
+
+@pytest.mark.parametrize("L,npole,c1", [((2, 2, 2, 4), 12, 0.0), ((4, 4, 4, 4), 6, -0.331)])
+def test_symplectic_md_parity(L, npole, c1):
+    """The exactly symplectic form of the step (momenta through dexp of the link rotation), float64,
+    against the oracle's symplectic_step."""
+    import paper_2112_04556_gb300 as rm
+    U = inputs.random_links(L, eps=0.3, seed=52)
+    P = inputs.gaussian_fields(L, 1, seed=53)[0]
+    m = fit.mass_term(npole, 0.9)
+    U_ref, P_ref, its = oracle.md_trajectory(L, U, P, 0.2, 3, 6.0, c1, m, tol=1e-14, fp_tol=1e-13, symplectic=True)
+    U_lf, P_lf, _ = oracle.md_trajectory(L, U, P, 0.2, 3, 6.0, c1, m, tol=1e-14, fp_tol=1e-13)
+    with rm.Context(L) as ctx:
+        Ud, Pd = dev(U), dev(P)
+        r = rm.md(ctx, Ud, Pd, _params(rm, m, c1=c1, nsteps=3, symplectic=True))
+    assert np.abs(host(Ud) - U_ref).max() <= 1e-11
+    assert rel_l2(host(Pd), P_ref) <= 1e-10
+    assert rel_l2(P_lf, P_ref) > 1e-4          # the two forms differ at O(eps) in the momenta
+    assert r["fp_iters_p"] > 0 and r["fp_iters_u"] > 0
+
+
+def test_symplectic_mixed_against_fp64_and_reversible():
+    """8^4, mixed precision (float32 Krylov, forces and dexp series; host-driven): the trajectory's dH
+    follows the float64 one, and forward, momentum flip, forward returns to the start."""
+    import paper_2112_04556_gb300 as rm
+    L = (8, 8, 8, 8)
+    U = inputs.random_links(L, eps=0.3, seed=75)
+    xi = inputs.gaussian_fields(L, 1, seed=76)[0]
+    P = inputs.gaussian_fields(L, 1, seed=77)[0]
+    m = rm.mass_fit(12, 0.9)
+    with rm.Context(L) as ctx:
+        out = {}
+        for prec in (rm.FP64, rm.MIXED):
+            tol = 1e-11 if prec == rm.FP64 else 1e-7
+            out[prec] = rm.rmhmc_trajectory(ctx, dev(U), _params(rm, m, tau=0.2, nsteps=4, prec=prec, tol_md=tol,
+                                                                 fp_tol=tol, metropolis=False, symplectic=True),
+                                            xi=dev(xi))
+        Ud, Pd = dev(U), dev(P)
+        p = _params(rm, m, tau=0.2, nsteps=4, prec=rm.MIXED, tol_md=1e-7, fp_tol=1e-7, symplectic=True)
+        rm.md(ctx, Ud, Pd, p)
+        Pd.neg_()
+        rm.md(ctx, Ud, Pd, p)
+        note = rm.tuning(ctx)
+    assert abs(out[rm.MIXED]["dH"] - out[rm.FP64]["dH"]) <= 1e-3, (out[rm.FP64]["dH"], out[rm.MIXED]["dH"])
+    assert np.abs(host(Ud) - U).max() <= 1e-5
+    assert np.abs(host(Pd) + P).max() <= 1e-4
+    assert "md graph captured" not in note      # the symplectic form runs host-driven
