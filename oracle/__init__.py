@@ -16,9 +16,14 @@ Carlo in lattice QCD", LATTICE2021 (arXiv:2112.04556).
   Sec. 2, Eq. (3): adjoint covariant Laplacian, normalised -Delta_G/16.
   Sec. 2, Eq. (4): per-mode power spectrum <F|B(lambda)|F> / Tr B(lambda),
                    B(lambda) = sum_i c_i T_i[-Delta_G/16].
-  Sec. 3, Eq. (5): H = 1/2 Tr P^dag M^{-1} P + S[U] (+ log|M|, not evaluated).
+  Sec. 3, Eq. (5): H = 1/2 Tr P^dag M^{-1} P + S[U]; the log|M| term through an
+                   auxiliary field (aux_mass, aux_action, potential_force).
   Sec. 3, Eq. (6): M = [c + rational function of -Delta_G/16]^{-2}.
-  Sec. 3: implicit (generalised) leapfrog of Girolami & Calderhead.
+  Sec. 3: implicit (generalised) leapfrog of Girolami & Calderhead with group
+          exponentials (leapfrog_step), and its exactly symplectic form on
+          T*SU(3) (symplectic_step, with ad, dexp_matrix, dexp, dexp_inv).
+  Sec. 4: Wilson flow and flowed energy (wilson_flow, flow_energy), band filters
+          as vectors (cheb_filter_apply), the mass fitted to a spectrum (fit.py).
 
 Parity pins: every function here is checked in tests/test_oracle_*.py against
 closed forms, invariants, dense linear algebra or finite differences.
