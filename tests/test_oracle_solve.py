@@ -158,3 +158,35 @@ def test_general_heatbath_kinetic_identity(oracle_lib):
     P = oracle_lib.heatbath(L, U, xi, mass, tol=1e-13)
     T, _, _ = oracle_lib.kinetic(L, U, P, mass, tol=1e-14)
     assert abs(T - 0.5 * np.sum(xi * xi)) < 1e-11 * T
+
+
+@pytest.mark.parametrize("symplectic", [False, True])
+def test_linearised_md_follows_the_discrete_oscillator(oracle_lib, symplectic):
+    """A weak transverse abelian wave b_mu(x) T^3 (amplitude 1e-6, P = 0) under the implicit leapfrog:
+    to first order in b the step is the plain leapfrog of the oscillator d^2 b/dtau^2 = -omega^2 b with
+    omega^2 = (beta/6) khat^2 R(lambda_k)^2 (M^{-1} = R^2 exactly, lambda_k = khat^2/16), whose
+    discrete solution from rest is b_n = b_0 cos(n theta), cos theta = 1 - (omega eps)^2 / 2.  Both
+    forms of the step (the dexp factors act at O(b^2))."""
+    L = (4, 4, 4, 4)
+    k = 2 * np.pi * np.array([1, 0, 0, 0]) / np.asarray(L)
+    sh = np.sin(k / 2)
+    e = np.array([0.0, 1.0, 0.0, 0.0])
+    b0 = 1e-6 * e[None, :] * np.cos((site_coords(L) @ k)[:, None] + k[None, :] / 2)
+    V = int(np.prod(L))
+    U = np.zeros((V, 4, 3, 3), dtype=np.complex128)
+    U[..., 0, 0] = np.exp(0.5j * b0)
+    U[..., 1, 1] = np.exp(-0.5j * b0)
+    U[..., 2, 2] = 1.0
+    P = np.zeros((V, 4, 8))
+    beta = 6.0
+    m = fit.mass_term(4, 0.9)
+    khat2 = np.sum(4 * sh ** 2)
+    omega = math.sqrt(beta / 6.0 * khat2) * float(fit.evaluate(m, khat2 / 16.0))
+    eps, n = 0.05, 12
+    theta = math.acos(1.0 - 0.5 * (omega * eps) ** 2)
+    U1, _, _ = oracle_lib.md_trajectory(L, U, P, eps * n, n, beta, 0.0, m, tol=1e-13, fp_tol=1e-16,
+                                        symplectic=symplectic)
+    b1 = np.angle(U1[..., 0, 0] / U1[..., 1, 1])
+    expect = b0 * math.cos(n * theta)
+    assert abs(math.cos(n * theta) - math.cos(n * eps * omega)) > 1e-3    # the discrete phase is resolved
+    assert np.abs(b1 - expect).max() < 1e-8 * np.abs(b0).max()
