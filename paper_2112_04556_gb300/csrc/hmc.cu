@@ -297,8 +297,10 @@ __global__ void k_mom_update(const double* __restrict__ P, double h, const doubl
 }
 
 // ------------------------------------------------------------------------------------------------
-// Exactly symplectic form of the step (rmhmc_params.symplectic): the momenta pass through the
-// right-trivialised derivative of the exponential, dexp_X = sum_n ad_X^n / (n+1)!, per link, with
+// Exactly symplectic form of Sec. 3's implicit leapfrog (rmhmc_params.symplectic): the generalised leapfrog
+// is symplectic Euler followed by its adjoint, and on the group each half is the discrete Legendre
+// transform of the discrete Lagrangian h L(U, xi), exp(i h xi) = U_{k+1} U_k^{-1}.  The momenta then pass
+// through the right-trivialised derivative of the exponential, dexp_X = sum_n ad_X^n / (n+1)!, per link, with
 // ad_X Y = coefficients of i[X.T, Y.T] = -f_abc X_a Y_b e_c (f the totally antisymmetric su(3)
 // structure constants).  The identity term is added in float64; the series terms are summed in TC
 // (float64 on the float64 path, float32 on the mixed one, where they are a correction of relative
