@@ -21,8 +21,6 @@
 
 namespace rm {
 
-constexpr int kSlotMax = 60;
-
 // ------------------------------------------------------------------------------------------------
 // exp(i Q) for Hermitian traceless Q by the Cayley-Hamilton theorem: exp(iQ) = f0 + f1 Q + f2 Q^2.
 // Small Q (c1 = Tr Q^2 / 2 < 1/4): the power series with Q^3 = c1 Q + c0 reducing every power.
