@@ -114,7 +114,7 @@ typedef struct {
                            P' = P + eps/2 F(U, P'), links U' = exp(i eps/2 V(U',P')) exp(i eps/2 V(U,P')) U);
                            1: its exactly symplectic form on T*SU(3), the same steps with the momenta passed
                            through the right-trivialised derivative of the exponential, per link
-                           dexp_X = sum_n ad_X^n/(n+1)!, X = eps/2 V:
+                           dexp_X = sum_n ad_X^n/(n+1)!, ad_X Y = coefficients of i[X.T, Y.T], X = eps/2 V:
                              dexp^{-1}_{X1} mu = P + eps/2 F(U, mu), X1 = eps/2 V(U, mu); B = exp(i X1) U;
                              P_h = dexp^{-1}_{-X1} mu;  dexp^{-1}_{X2} mu2 = P_h, X2 = eps/2 V(U', mu2),
                              U' = exp(i X2) B;  P'' = dexp^{-1}_{-X2} mu2 + eps/2 F(U', mu2).
