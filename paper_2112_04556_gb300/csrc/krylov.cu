@@ -1,5 +1,7 @@
-// Krylov engine (see krylov.cuh): CG on the smallest shift keeping the residual basis in HBM,
-// Lanczos post-processing on the host, basis combinations, float64 reliable updates.
+// Krylov engine (see krylov.cuh) for the rational mass term of Sec. 3, Eq. (6): the shifted solves
+// (A + sigma_j)^{-1} b of R(A) = c + sum_j alpha_j / (A + sigma_j) by CG on the smallest shift keeping
+// the residual basis in HBM, Lanczos post-processing on the host, basis combinations, float64 reliable
+// updates.
 #include <math.h>
 #include <string.h>
 

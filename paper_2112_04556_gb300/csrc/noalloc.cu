@@ -1,5 +1,6 @@
-// Gauge action and average plaquette without any allocation: a variant of the action reduction of
-// gauge.cu for callers that may not allocate device memory.
+// Gauge action (Sec. 2: Wilson plaquettes plus weighted 1x2 rectangles) and average plaquette without
+// any allocation: a variant of the action reduction of gauge.cu for callers that may not allocate
+// device memory.
 //
 // Who needs this: code that is capturing a CUDA graph (cudaMalloc/cudaFree are not capturable and
 // synchronise the device), and applications whose device memory is entirely reserved by another

@@ -1,5 +1,6 @@
 // Counter-based generator Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), host and device,
-// and the Gaussian / uniform draws built on it.
+// and the Gaussian / uniform draws built on it: the momentum refresh and the Metropolis test of Sec. 3
+// and the noise vectors of the trace in Eq. (4).
 //   block: counter {c0, c1, c2, c3}, key {k0, k1}; ten rounds, key bumped by the Weyl constants
 //   between rounds.  Uniforms take 53 bits from two 32-bit words and lie in (0, 1].
 #pragma once

@@ -1,4 +1,5 @@
-// Device SU(3) / su(3) algebra for the hot path, templated on the real type (float or double).
+// Device SU(3) / su(3) algebra for the hot path (the links and su(3)-valued fields of Sec. 2),
+// templated on the real type (float or double).
 //
 // su(3) elements travel as 8 coefficients p^a of P = sum_a p^a T^a, T^a = lambda^a / 2.  Inside the
 // stencil they are expanded to a "doubled" Hermitian matrix 2P (3 real diagonal entries and the
