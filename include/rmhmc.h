@@ -262,15 +262,17 @@ int rmhmc_mass_fit_spectrum(int nwin, const double* lam, const double* spec, int
                             double sigma_max, double* c, double* alpha, double* sigma, double* max_rel_err);
 
 /* Allocation-free gauge action: the paper has no counterpart; this is a service for callers that cannot
- * allocate device memory -- code that is capturing a CUDA graph (cudaMalloc is not capturable) or an
- * application whose device memory is entirely reserved by another allocator.  No context is needed and
- * nothing is allocated: U (device, canonical complex128 [V][4][3][3]) and out (device, 2 doubles:
- * out[0] = S as in gauge_force, out[1] = average plaquette ReTr P/3) are the caller's; the only scratch is
- * a ~64 KB file-scope device array inside the library, kept by every GPU that loads the library until
- * the process exits.  Its device address is looked up by the first call made on each device, so make that
- * first call outside any stream capture.  Calls share that array: calls that overlap on the GPU (e.g.
- * on two unordered streams) race and must not be issued.  Asynchronous on `stream`.  Returns
- * RMHMC_EINVAL for a NULL or misaligned pointer, an extent < 2, or more than 2^26 sites. */
+ * allocate device memory -- an application whose device memory is entirely handed out by another
+ * allocator (a caching pool that reserved the GPU), or code on a latency-critical path that must not call
+ * cudaMalloc/cudaFree because they synchronise the device.  No context is needed and nothing is
+ * allocated: U (device, canonical complex128 [V][4][3][3]) and out (device, 2 doubles: out[0] = S as in
+ * gauge_force, out[1] = average plaquette ReTr P/3) are the caller's; the only scratch is a ~64 KB
+ * file-scope device array inside the library (4096 block partials and a counter), kept by every GPU that
+ * loads the library until the process exits.  Its device address is looked up by the first call made on
+ * each device, so make that first call before any stream capture.  Calls share that array and each call
+ * clears its counter: calls that overlap on the GPU (e.g. on two unordered streams) race and must not be
+ * issued.  Asynchronous on `stream`.  Returns RMHMC_EINVAL for a NULL or misaligned pointer, an extent
+ * < 2 or > 2^26, or more than 2^26 sites. */
 int rmhmc_action_noalloc(const int dims[4], const double* U, double beta, double c1, double* out,
                          cudaStream_t stream);
 

@@ -115,12 +115,13 @@ using namespace rm;
 extern "C" int rmhmc_create(const int dims[4], int device, rmhmc_ctx** out) {
     if (!dims || !out) return RMHMC_EINVAL;
     *out = nullptr;
+    // every partial product is checked against the limit, so no extent can overflow the product
     long long V = 1;
     for (int d = 0; d < 4; d++) {
-        if (dims[d] < 2) return RMHMC_EINVAL;
+        if (dims[d] < 2 || dims[d] > (1 << 26)) return RMHMC_EINVAL;
         V *= dims[d];
+        if (V > (1ll << 26)) return RMHMC_EINVAL;   // site indices stay well inside int
     }
-    if (V > (1ll << 26)) return RMHMC_EINVAL;   // site indices stay well inside int
     if (cudaSetDevice(device) != cudaSuccess) return RMHMC_ECUDA;
     rmhmc_ctx* ctx = new rmhmc_ctx();
     ctx->device = device;

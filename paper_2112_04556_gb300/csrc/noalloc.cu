@@ -2,17 +2,18 @@
 // any allocation: a variant of the action reduction of gauge.cu for callers that may not allocate
 // device memory.
 //
-// Who needs this: code that is capturing a CUDA graph (cudaMalloc/cudaFree are not capturable and
-// synchronise the device), and applications whose device memory is entirely reserved by another
-// allocator, so that a context's workspace cannot be created.  Such a caller passes the links and a
-// two-double output buffer it already owns; the only scratch is the file-scope device array below.
+// Who needs this: a caller whose device memory is entirely handed out by another allocator (a framework's
+// caching pool that reserved the whole GPU up front), so that a context's workspace cannot be created, or
+// a caller on a latency-critical path that must not call cudaMalloc/cudaFree because they synchronise the
+// device.  Such a caller passes the links and a two-double output buffer it already owns; the only scratch
+// is the file-scope device array below.
 //
 // The scratch holds kNoAllocBlocks block partials and a ticket counter.  It is shared by every call in
 // the process and keeps the previous call's contents: each call zeroes the counter before its kernel,
 // and two calls that overlap on the GPU (different streams, no ordering) race on it and must not be
 // issued.  Each GPU that loads the library keeps this ~64 KB array until the process exits.  The device
 // address of the array is looked up once per device (cudaGetSymbolAddress) by the first call made with
-// that device current; make that first call outside any stream capture.
+// that device current; make that first call before any stream capture.
 #include <mutex>
 
 #include "common.cuh"
@@ -124,12 +125,13 @@ using namespace rm;
 extern "C" int rmhmc_action_noalloc(const int dims[4], const double* U, double beta, double c1, double* out,
                                     cudaStream_t stream) {
     if (!dims || !U || !out) return RMHMC_EINVAL;
+    // the largest lattice: 2^26 sites; each partial product is checked, so no extent overflows it
     long long V = 1;
     for (int d = 0; d < 4; d++) {
-        if (dims[d] < 2) return RMHMC_EINVAL;
+        if (dims[d] < 2 || dims[d] > (1 << 26)) return RMHMC_EINVAL;
         V *= dims[d];
+        if (V > (1ll << 26)) return RMHMC_EINVAL;
     }
-    if (V > (1ll << 26)) return RMHMC_EINVAL;     // the largest lattice: 2^26 sites
     if ((uintptr_t)U % 16) return RMHMC_EINVAL;
     Geom g{};
     for (int d = 0; d < 4; d++) g.L[d] = dims[d];

@@ -120,3 +120,19 @@ def test_weak_field_linear_response(oracle_lib, n, e):
     assert np.abs(F[:, :, 2] - expect).max() < 1e-6 * np.abs(expect).max()
     others = np.delete(F, 2, axis=2)
     assert np.abs(others).max() < 1e-12
+
+
+@pytest.mark.parametrize("L", [ASYM, (3, 4, 3, 6)])
+@pytest.mark.parametrize("c1", [0.0, -0.331])
+def test_site_sampled_force_equals_full(oracle_lib, L, c1):
+    """The site-sampled gauge force (the reference of the full-size parity tests) equals the full force,
+    which the pins above fix, at every site, visited in a shuffled order with repeats; the odd extent 3
+    makes the rectangles' two-step reach wrap onto the starting site's neighbourhood."""
+    V = int(np.prod(L))
+    U = inputs.random_links(L, eps=0.8, seed=31)
+    full = oracle_lib.gauge_force(L, U, 6.0, c1)
+    rng = np.random.default_rng(32)
+    sites = np.concatenate([rng.permutation(V), rng.integers(0, V, 13)]).astype(np.int64)
+    F = oracle_lib.gauge_force_sites(L, U, 6.0, c1, sites)
+    assert F.shape == (len(sites), 4, 8)
+    assert np.array_equal(F, full[sites])

@@ -122,3 +122,19 @@ def test_link_gradient_finite_difference(oracle_lib):
     G2 = oracle_lib.lap_link_grad(L, U, np.stack([X, X2]), np.stack([Z, Z2]), [0.3, -1.7])
     ref = 0.3 * G - 1.7 * oracle_lib.lap_link_grad(L, U, X2, Z2, [1.0])
     assert np.abs(G2 - ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("L", [ASYM, (3, 4, 3, 6)])
+def test_site_sampled_form_equals_full(oracle_lib, L):
+    """The site-sampled A X (the reference of the full-size parity tests) equals the full application,
+    which the pins above fix, at every site of the lattice, visited in a shuffled order with repeats;
+    odd extents exercise the periodic wrap at both ends."""
+    V = int(np.prod(L))
+    U = inputs.random_links(L, eps=0.7, seed=21)
+    X = inputs.gaussian_fields(L, 1, seed=22)[0]
+    full = oracle_lib.lap(L, U, X)
+    rng = np.random.default_rng(23)
+    sites = np.concatenate([rng.permutation(V), rng.integers(0, V, 17)]).astype(np.int64)
+    Y = oracle_lib.lap_sites(L, U, X, sites)
+    assert Y.shape == (len(sites), 4, 8)
+    assert np.array_equal(Y, full[sites])
