@@ -41,6 +41,17 @@ NSTEPS = 20
 CHEB_DEGREE = 200
 CHEB_WINDOWS = 64
 CHEB_NOISE = 16
+# mixed-precision MD settings of the headline: float32 Krylov forces to MIXED_TOL_MD, fixed points to a max-norm
+# change of MIXED_FP_TOL followed by MIXED_FP_EXTRA further iterations, which remove the systematic part of
+# the fixed points' error (float32 rounding noise stays); float64 runs use FP64_TOL for both
+MIXED_TOL_MD = 3e-7
+MIXED_FP_TOL = 1e-6
+MIXED_FP_EXTRA = 3
+FP64_TOL = 1e-10
+DH_BAR = 1e-3
+# step count of the accepting setting at 32^4 (tau = 1): <dH> = 200 at 20 steps and falls as eps^4 (the spread
+# of dH across trajectories, ~20, obeys <dH> = sigma^2/2), so 80 steps give <dH> ~ 0.8, acceptance ~ 0.5
+ACCEPT_NSTEPS = 80
 # DRAM bytes (read + write) of one k_cg_A<float,18> launch at 32^4 with k > 0, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_cg_A_fp32_32x32x32x32.md), per tuned launch shape
 # (components per lane, threads per block); a shape without a capture reports null
@@ -49,6 +60,9 @@ CG_TRAFFIC_32 = {(2, 256): 846.0e6}
 # read r_k (128 B) and q_{k-1} (128 B), write q_k (128 B), four links of 72 B
 CG_BYTES_PER_SITE = 3 * 128 + 4 * 72
 IWASAKI_C1 = -0.331
+# float32 FMA rate of the GB300 (measured with a register-resident FMA loop on this machine: 37.4 TFMA/s; the nominal
+# 152 SMs x 128 lanes x 2.07 GHz = 40.3 TFMA/s)
+FP32_FMA_PEAK = 37.4
 
 
 def measured_peaks():
@@ -190,6 +204,71 @@ def run_reference(args, rank, world):
     return 0
 
 
+# algorithmic bytes per site of lap_apply: links once (4 x 18 or 12 reals) + every field read once and written
+# once (2 x 32 reals per field)
+def lap_bytes_per_site(prec_bytes, linkfmt, nf):
+    return 4 * linkfmt * prec_bytes + 2 * 32 * prec_bytes * nf
+
+
+def lap_fma_per_site(form, nf, linkfmt=18):
+    """FP32 pipe operations (FMA, or a single add or multiply) per site: the 3x3 form does 8 hops x 4 components
+    x 144 FMA per field (+24 per hop to rebuild the third row of 12-real links); the adjoint form builds 8
+    adjoint matrices (~270 operations each, +24 for 12-real links) and does 64 FMA per component hop."""
+    if form == "3x3":
+        return 4608 * nf + (8 * 24 if linkfmt == 12 else 0)
+    return 8 * (270 + (24 if linkfmt == 12 else 0)) + 8 * 4 * 64 * nf
+
+
+def lap_block(rm, torch, inputs, dims, ctx=None, U=None, reps=20):
+    """lap_apply timed with CUDA events on the launching stream (warm-up 3, then reps calls): float32 with 18-
+    and 12-real links, float64, and four float32 fields in one launch (the adjoint form).  The inputs (links
+    and fields) are larger than L2 at these sizes, so no flush is needed between calls."""
+    import numpy as np
+    V = int(np.prod(dims))
+    own = ctx is None
+    if own:
+        ctx = rm.Context(dims)
+        U = torch.from_numpy(inputs.random_links(dims, eps=0.3, seed=0)).cuda()
+    rm.set_links(ctx, U)
+    X64 = torch.from_numpy(inputs.gaussian_fields(dims, 1, seed=1)[0]).cuda()
+    X32 = X64.float()
+    X4 = torch.from_numpy(inputs.gaussian_fields(dims, 4, seed=2)).cuda().float()
+    peak, kind = measured_peaks()
+    out = {"lattice": "x".join(map(str, dims)), "peak_gbs": peak, "peak_kind": kind, "fp32_fma_peak_tfma_s": FP32_FMA_PEAK,
+           "l2": "inputs larger than L2, no flush", "variants": []}
+    st = torch.cuda.current_stream()
+    for name, X, prec, lf, nf, form in [("fp32_18", X32, rm.FP32, 18, 1, "3x3"), ("fp32_12", X32, rm.FP32, 12, 1, "3x3"),
+                                        ("fp64_18", X64, rm.FP64, 18, 1, "3x3"),
+                                        ("fp32_18_x4", X4, rm.FP32, 18, 4, "adjoint")]:
+        Y = torch.empty_like(X)
+        for _ in range(3):
+            rm.lap_apply(ctx, None, X, Y, prec=prec, linkfmt=lf)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            rm.lap_apply(ctx, None, X, Y, prec=prec, linkfmt=lf)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        pb = 8 if prec == rm.FP64 else 4
+        gbs = lap_bytes_per_site(pb, lf, nf) * V / (ms * 1e-3) / 1e9
+        fma = lap_fma_per_site(form, nf, lf) * V / (ms * 1e-3) / 1e12
+        d = {"variant": name, "ms": ms, "bytes_per_site": lap_bytes_per_site(pb, lf, nf), "gbs_alg": gbs,
+             "frac_hbm": gbs / peak, "form": form}
+        if prec == rm.FP32:
+            d["tfma_s"] = fma
+            d["frac_fp32_fma"] = fma / FP32_FMA_PEAK
+        else:
+            d["tflop_s_fp64"] = 2 * fma
+        out["variants"].append(d)
+        del Y
+    if own:
+        ctx.close()
+    return out
+
+
 def run_kernel(args):
     """Kernel microbenchmark: lap_apply (float32, 18-real links) or one mixed kinetic-force evaluation
     (the conjugate-gradient stencil in the tuned shape) on the chosen lattice, timed with CUDA events."""
@@ -255,6 +334,8 @@ def main():
     ap.add_argument("--graphs", choices=["on", "off"], default="on",
                     help="run the mixed-precision MD as one CUDA graph per trajectory")
     ap.add_argument("--no-parity", action="store_true", help="skip the small-step float64-vs-mixed dH parity pair")
+    ap.add_argument("--no-lap", action="store_true", help="skip the lap_apply block")
+    ap.add_argument("--no-accept", action="store_true", help="skip the accepting-setting trajectories")
     ap.add_argument("--compare-tau", type=float, default=TAU,
                     help="trajectory length of the float64-vs-mixed comparison (same number of steps)")
     args = ap.parse_args()
@@ -300,22 +381,34 @@ def main():
                            prec=rm.MIXED, seed=seeds["therm"], traj_index=1000 + n, metropolis=False)
         therm.append(rm.rmhmc_trajectory(lat, U, p)["plaq"])
 
-    def params(idx, prec, tau=TAU):
-        return rm.make_params(beta=BETA, mass=mass, tau=tau, nsteps=args.nsteps,
-                              tol_md=1e-6 if prec == rm.MIXED else 1e-10, tol_h=1e-12,
-                              fp_tol=1e-6 if prec == rm.MIXED else 1e-10, fp_maxit=50, maxiter=400, prec=prec,
-                              seed=seeds["traj"], traj_index=idx, metropolis=True)
+    def params(idx, prec, tau=TAU, nsteps=None, metropolis=True):
+        mixed = prec == rm.MIXED
+        return rm.make_params(beta=BETA, mass=mass, tau=tau, nsteps=nsteps or args.nsteps,
+                              tol_md=MIXED_TOL_MD if mixed else FP64_TOL, tol_h=1e-12,
+                              fp_tol=MIXED_FP_TOL if mixed else FP64_TOL, fp_extra=MIXED_FP_EXTRA if mixed else 0,
+                              fp_maxit=50, maxiter=400, prec=prec, seed=seeds["traj"], traj_index=idx,
+                              metropolis=metropolis)
 
     F2 = torch.empty((2, V, 4, 8), dtype=torch.float64, device="cuda")
     edges = inputs.equal_windows(CHEB_WINDOWS)
     results = []
+    ev = {"traj": [], "spec": []}
 
-    def step(idx, Ulinks):
+    def step(idx, Ulinks, timed=False):
+        if timed:
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
         r = rm.rmhmc_trajectory(lat, Ulinks, params(idx, rm.MIXED))
+        if timed:
+            b.record(stream)
         rm.gauge_force(lat, None, BETA, 0.0, prec=rm.FP32, F=F2[0])
         rm.gauge_force(lat, None, BETA, IWASAKI_C1, prec=rm.FP32, F=F2[1])
         spec = rm.cheb_filter_spectrum(lat, None, F2, None, CHEB_DEGREE, edges, prec=rm.MIXED,
                                        nnoise=CHEB_NOISE, seed=idx)[0]
+        if timed:
+            c.record(stream)
+            ev["traj"].append((a, b))
+            ev["spec"].append((b, c))
         r["spec_low"] = float(spec[0, 0])
         r["spec_high"] = float(spec[0, -1])
         return r
@@ -335,7 +428,7 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(args.steps):
-        results.append(step(args.warmup + k, U))
+        results.append(step(args.warmup + k, U, timed=True))
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -344,6 +437,9 @@ def main():
     cnt = rm.counters(lat, reset=True)
     ms = max_over_ranks(ms, dist, "cuda")
     value = world * args.steps / (ms / 1e3)
+    split = {"trajectory_s": sum(a.elapsed_time(b) for a, b in ev["traj"]) / 1e3 / args.steps,
+             "spectrum_s": sum(a.elapsed_time(b) for a, b in ev["spec"]) / 1e3 / args.steps}
+    split["traj_per_s_trajectory_only"] = 1.0 / split["trajectory_s"]
 
     # live roofline of the conjugate-gradient stencil (float32, 18-real links):
     # per site 3 field passes of 128 B (read r_k and q_{k-1}, write q_k) + 4 links x 72 B = 672 B
@@ -359,7 +455,7 @@ def main():
                 "frac": achieved / peak if achieved else None, "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": "k_cg_A<float,18> (CG stencil)", "shape": shape, "launches": cnt["cg_count"],
                 "avg_launch_ms": cg_avg_ms, "alu_tfma_s": alu_fma / (cg_avg_ms * 1e-3) / 1e12 if cnt["cg_count"] else None,
-                "alu_peak_tfma_s": 37.4}
+                "alu_peak_tfma_s": FP32_FMA_PEAK}
 
     # end to end through the public API with host buffers: pinned H2D of the links, D2H of the result
     e2e = None
@@ -382,35 +478,54 @@ def main():
         e2e = {"value": world * args.steps / sec, "unit": "traj/s", "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb + 8 * 16}
 
-    # mixed vs float64 at fixed dH: both from the same links and momenta
+    # the Laplacian (first half of the metric): 32^4 on the workload's thermalised links, and 24^3 x 48
+    lap = None
+    if rank == 0 and not args.no_lap:
+        lap = [lap_block(rm, torch, inputs, DIMS, lat, U)]
+        if DIMS == (32, 32, 32, 32):
+            lap.append(lap_block(rm, torch, inputs, (24, 24, 24, 48)))
+
+    def timed_traj(Ulinks, p):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = rm.rmhmc_trajectory(lat, Ulinks, p)
+        torch.cuda.synchronize()
+        r["seconds"] = time.perf_counter() - t0
+        return r
+
+    # mixed vs float64 at fixed dH: both from the same links and momenta, the headline's settings
     fp64 = None
     if world == 1 and not args.no_fp64:
-        Ua, Ub = U_start.clone(), U_start.clone()
-        t0 = time.perf_counter()
-        ra = rm.rmhmc_trajectory(lat, Ua, params(0, rm.FP64, args.compare_tau))
-        torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
-        rb = rm.rmhmc_trajectory(lat, Ub, params(0, rm.MIXED, args.compare_tau))
+        ra = timed_traj(U_start.clone(), params(0, rm.FP64, args.compare_tau))
+        rb = timed_traj(U_start.clone(), params(0, rm.MIXED, args.compare_tau))
+        d = abs(ra["dH"] - rb["dH"])
         fp64 = {"tau": args.compare_tau, "nsteps": args.nsteps,
-                "traj_per_s_fp64": 1.0 / t64, "dH_fp64": ra["dH"], "dH_mixed": rb["dH"],
-                "abs_dH_diff": abs(ra["dH"] - rb["dH"]), "plaq_fp64": ra["plaq"], "plaq_mixed": rb["plaq"],
-                "md_iters_fp64": ra["md_iters"], "md_iters_mixed": rb["md_iters"]}
-        # the |dH| parity of the mixed path where dH = O(0.1): tau = 0.1 in the same 20 steps, mixed forces to
-        # 3e-7 and fixed points to 1e-8 (float32 forces allow no tighter fixed points at this step size)
+                "mixed": {"tol_md": MIXED_TOL_MD, "fp_tol": MIXED_FP_TOL, "fp_extra": MIXED_FP_EXTRA},
+                "fp64": {"tol_md": FP64_TOL, "fp_tol": FP64_TOL},
+                "traj_per_s_fp64": 1.0 / ra["seconds"], "seconds_fp64": ra["seconds"], "seconds_mixed": rb["seconds"],
+                "speedup_mixed_over_fp64": ra["seconds"] / rb["seconds"],
+                "dH_fp64": ra["dH"], "dH_mixed": rb["dH"], "abs_dH_diff": d, "dH_bar": DH_BAR,
+                "meets_dH_bar": bool(d <= DH_BAR), "plaq_fp64": ra["plaq"], "plaq_mixed": rb["plaq"],
+                "md_iters_fp64": ra["md_iters"], "md_iters_mixed": rb["md_iters"],
+                "fp_iters_fp64": [ra["fp_iters_p"], ra["fp_iters_u"]], "fp_iters_mixed": [rb["fp_iters_p"], rb["fp_iters_u"]]}
+        # the same pair where dH = O(0.1): tau = 0.1 in the same 20 steps
         if not args.no_parity:
-            def pp(prec, tol_md, fp_tol):
-                return rm.make_params(beta=BETA, mass=mass, tau=0.1, nsteps=args.nsteps, tol_md=tol_md, tol_h=1e-12,
-                                      fp_tol=fp_tol, fp_maxit=50, maxiter=400, prec=prec, seed=seeds["traj"],
-                                      traj_index=0, metropolis=False)
-            Ua, Ub = U_start.clone(), U_start.clone()
-            ra = rm.rmhmc_trajectory(lat, Ua, pp(rm.FP64, 1e-10, 1e-10))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            rb = rm.rmhmc_trajectory(lat, Ub, pp(rm.MIXED, 3e-7, 1e-8))
-            torch.cuda.synchronize()
-            fp64["small_step"] = {"tau": 0.1, "nsteps": args.nsteps, "mixed_tol_md": 3e-7, "mixed_fp_tol": 1e-8,
-                                  "dH_fp64": ra["dH"], "dH_mixed": rb["dH"], "abs_dH_diff": abs(ra["dH"] - rb["dH"]),
-                                  "mixed_seconds": time.perf_counter() - t0}
+            ra = timed_traj(U_start.clone(), params(0, rm.FP64, 0.1, metropolis=False))
+            rb = timed_traj(U_start.clone(), params(0, rm.MIXED, 0.1, metropolis=False))
+            fp64["small_step"] = {"tau": 0.1, "nsteps": args.nsteps, "dH_fp64": ra["dH"], "dH_mixed": rb["dH"],
+                                  "abs_dH_diff": abs(ra["dH"] - rb["dH"]), "seconds_fp64": ra["seconds"],
+                                  "seconds_mixed": rb["seconds"], "speedup_mixed_over_fp64": ra["seconds"] / rb["seconds"]}
+
+    # an accepting setting at 32^4: tau = 1 in ACCEPT_NSTEPS steps (mixed, the headline's tolerances), from the
+    # same start, two trajectories with Metropolis
+    accept = None
+    if rank == 0 and not args.no_accept:
+        Ua = U_start.clone()
+        runs = [timed_traj(Ua, params(20000 + i, rm.MIXED, TAU, ACCEPT_NSTEPS)) for i in range(2)]
+        accept = {"tau": TAU, "nsteps": ACCEPT_NSTEPS, "dH": [r["dH"] for r in runs],
+                  "accepted": [r["accepted"] for r in runs], "seconds": [r["seconds"] for r in runs],
+                  "traj_per_s": 2.0 / sum(r["seconds"] for r in runs),
+                  "acceptance_expected": [min(1.0, math.exp(-r["dH"])) for r in runs]}
 
     if rank != 0:
         return 0
@@ -421,7 +536,9 @@ def main():
             "thermalisation_plaq": therm[-3:] if therm else None,
             "autotune": rm.tuning(lat),
             "roofline": roofline, "clocks": clk, "gpu_launches": cnt["launches"],
-            "krylov_iters": cnt["krylov_iters"], "e2e": e2e,
+            "krylov_iters": cnt["krylov_iters"], "e2e": e2e, "split": split, "lap_apply": lap,
+            "accepting": accept,
+            "mixed_settings": {"tol_md": MIXED_TOL_MD, "fp_tol": MIXED_FP_TOL, "fp_extra": MIXED_FP_EXTRA},
             "trajectories": [{k: r[k] for k in ("dH", "accepted", "plaq", "md_solves", "md_iters", "fp_iters_p",
                                                 "fp_iters_u", "spec_low", "spec_high")} for r in results]}
     if fp64:

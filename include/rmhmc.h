@@ -121,6 +121,15 @@ typedef struct {
                            It preserves phase-space volume exactly (the first form only to O(eps^3) per step
                            with a link-dependent mass).  Host-driven MD only (no graph); dexp series in float64
                            (float32 corrections on the mixed path).  Any other value: RMHMC_EINVAL. */
+    int fp_extra;       /* fixed-point iterations run after the max-norm change first falls to fp_tol (0: stop
+                           there; 0 <= fp_extra < fp_maxit, which counts every iteration).  With float32 forces
+                           the change cannot fall much below the forces' rounding noise, while the error the
+                           iteration has left shrinks by the contraction factor at every further iteration:
+                           extra iterations remove that systematic part, so the mixed trajectory follows the
+                           float64 one to the noise level. */
+    int fg_fp64;        /* gauge force inside the mixed-precision MD: 0 float32 staples from the float32 link
+                           copies, 1 float64 staples from the float64 links (the float64 MD always uses float64);
+                           any other value: RMHMC_EINVAL */
 } rmhmc_params;
 
 typedef struct {
@@ -221,17 +230,18 @@ int cheb_filter_spectrum(rmhmc_ctx* ctx, const double* U, const double* F, int n
 /* Sec. 3, Eq. (6): rational mass term via a multishift Krylov solve                                */
 /* ---------------------------------------------------------------------------------------------- */
 
-/* y = c b + sum_j alpha[j] (A + sigma[j])^{-1} b for one field b (device float64 [V][4][8]),
- * nshift shifts (host sigma[], alpha[], every sigma > 0).  All shifts share one Krylov space
- * (multishift CG).  Stops when every shift has relative true residual
- * |b - (A+sigma_j) x_j| / |b| <= tol (checked in float64), or returns RMHMC_ENOCONV after maxiter
- * Krylov iterations in total.
+/* y_f = c b_f + sum_j alpha[j] (A + sigma[j])^{-1} b_f for nfield fields b_f (Sec. 3, Eq. 6: the rational
+ * mass term; device float64 [nfield][V][4][8]), nshift shifts (host sigma[], alpha[], every sigma > 0).  For
+ * each field all shifts share one Krylov space (multishift CG); the fields are solved one after the other
+ * with one workspace.  Stops when every shift of a field has relative true residual
+ * |b_f - (A+sigma_j) x_fj| / |b_f| <= tol (checked in float64), or returns RMHMC_ENOCONV once a field's
+ * solve exceeds maxiter Krylov iterations.
  * prec = RMHMC_FP64: float64 throughout.  prec = RMHMC_MIXED: float32 Krylov iterations, then
- * float64 reliable updates (true residual per shift) with float32 correction solves until tol.
- * Outputs: y (device float64 [V][4][8]); xs (device float64 [nshift][V][4][8], nullable);
- * iters (host, nullable) Krylov iterations in total; resid (host [nshift], nullable) final true
- * relative residuals. */
-int rat_mass_solve(rmhmc_ctx* ctx, const double* U, const double* b, int nshift,
+ * float64-accurate reliable updates (true residual per shift) with float32 correction solves until tol.
+ * Outputs: y (device float64 [nfield][V][4][8]); xs (device float64 [nfield][nshift][V][4][8], nullable);
+ * iters (host, nullable) Krylov iterations summed over the fields; resid (host [nfield][nshift],
+ * nullable) final true relative residuals.  nfield = 0 does nothing. */
+int rat_mass_solve(rmhmc_ctx* ctx, const double* U, const double* b, int nfield, int nshift,
                    const double* sigma, const double* alpha, double c, double tol, int maxiter,
                    int prec, double* y, double* xs, int* iters, double* resid, cudaStream_t stream);
 

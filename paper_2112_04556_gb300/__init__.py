@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
                 ("nsteps", ctypes.c_int), ("tol_md", ctypes.c_double), ("tol_h", ctypes.c_double),
                 ("fp_tol", ctypes.c_double), ("fp_maxit", ctypes.c_int), ("maxiter", ctypes.c_int),
                 ("prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("traj_index", ctypes.c_uint32),
-                ("metropolis", ctypes.c_int), ("logdet", ctypes.c_int), ("symplectic", ctypes.c_int)]
+                ("metropolis", ctypes.c_int), ("logdet", ctypes.c_int), ("symplectic", ctypes.c_int),
+                ("fp_extra", ctypes.c_int), ("fg_fp64", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -81,7 +82,7 @@ def lib():
         "lap_apply": ([P, P, P, P, I, I, I, I, P], I),
         "lap_link_grad": ([P, P, P, P, I, DP, I, P, P], I),
         "cheb_filter_spectrum": ([P, P, P, I, P, I, ctypes.c_uint64, I, I, DP, I, I, DP, DP, DP, DP, P], I),
-        "rat_mass_solve": ([P, P, P, I, DP, DP, D, D, I, I, P, P, ctypes.POINTER(I), DP, P], I),
+        "rat_mass_solve": ([P, P, P, I, I, DP, DP, D, D, I, I, P, P, ctypes.POINTER(I), DP, P], I),
         "rmhmc_heatbath": ([P, P, P, ctypes.POINTER(Mass), D, I, P, P], I),
         "rmhmc_mass_fit": ([I, D, DP, DP, DP, DP], I),
         "gauge_force": ([P, P, D, D, I, P, DP, DP, P], I),
@@ -278,19 +279,26 @@ def _mass_struct(mass):
 
 
 def rat_mass_solve(ctx, U, b, mass, tol=1e-10, maxiter=2000, prec=FP64, want_xs=False, stream=None):
-    """y = c b + sum_j alpha_j (A + sigma_j)^{-1} b.  Returns (y, xs or None, iters, resid[nshift])."""
+    """y = c b + sum_j alpha_j (A + sigma_j)^{-1} b for b [V,4,8] or nfield fields [nfield,V,4,8].
+    Returns (y, xs or None ([nshift,..] per field), iters summed over fields, resid[nshift] or [nfield,nshift])."""
     import torch
     alpha, ap = _dbl(mass["alpha"])
     sigma, sp = _dbl(mass["sigma"])
     n = len(alpha)
+    nfield = b.numel() // (ctx.V * 32)
+    single = b.dim() == 3
     y = torch.empty_like(b)
-    xs = torch.empty((n,) + tuple(b.shape), dtype=b.dtype, device=b.device) if want_xs else None
+    xs = None
+    if want_xs:
+        shape = (n,) + tuple(b.shape) if single else (nfield, n) + tuple(b.shape[1:])
+        xs = torch.empty(shape, dtype=b.dtype, device=b.device)
     iters = ctypes.c_int()
-    resid = np.zeros(max(n, 1))
-    ctx.check(lib().rat_mass_solve(ctx.h, _links(U), _ptr(b), n, sp, ap, float(mass["c"]), float(tol), int(maxiter),
-                                   int(prec), _ptr(y), _ptr(xs), ctypes.byref(iters),
+    resid = np.zeros(max(n * nfield, 1))
+    ctx.check(lib().rat_mass_solve(ctx.h, _links(U), _ptr(b), nfield, n, sp, ap, float(mass["c"]), float(tol),
+                                   int(maxiter), int(prec), _ptr(y), _ptr(xs), ctypes.byref(iters),
                                    resid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)))
-    return y, xs, iters.value, resid[:n]
+    res = resid[:n] if single else resid[:n * nfield].reshape(nfield, n)
+    return y, xs, iters.value, res
 
 
 def heatbath(ctx, U, xi, mass, tol=1e-10, prec=FP64, stream=None):
@@ -421,12 +429,12 @@ def wilson_flow(ctx, U, eps, nsteps, prec=FP64, stream=None):
 
 def make_params(beta=6.0, c1=0.0, mass=None, tau=1.0, nsteps=20, tol_md=1e-10, tol_h=1e-11, fp_tol=1e-10,
                 fp_maxit=50, maxiter=2000, prec=FP64, seed=0, traj_index=0, metropolis=True, logdet=False,
-                symplectic=False):
+                symplectic=False, fp_extra=0, fg_fp64=False):
     mass = mass if mass is not None else {"c": 1.0, "alpha": [], "sigma": [], "kappa": 0.0}
     ms = _mass_struct(mass)
     p = Params(float(beta), float(c1), ms, float(tau), int(nsteps), float(tol_md), float(tol_h),
                float(fp_tol), int(fp_maxit), int(maxiter), int(prec), int(seed), int(traj_index), int(bool(metropolis)),
-               int(bool(logdet)), int(bool(symplectic)))
+               int(bool(logdet)), int(bool(symplectic)), int(fp_extra), int(bool(fg_fp64)))
     p._keep = ms._keep   # the struct copy holds raw pointers into these arrays
     return p
 

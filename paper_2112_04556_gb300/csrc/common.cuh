@@ -68,6 +68,19 @@ __device__ __forceinline__ void site_coords(const Geom& g, int s, int c[4]) {
     }
 }
 
+// neighbour of site s one step (n = +1 or -1) along direction d, periodic
+__device__ __forceinline__ int step_site(const Geom& g, int s, int d, int n) {
+    int r = s, c = 0;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        const int q = fast_div(g, r, e);
+        if (e == d) c = r - q * g.L[e];
+        r = q;
+    }
+    if (n > 0) return c == g.L[d] - 1 ? s - c * g.stride[d] : s + g.stride[d];
+    return c == 0 ? s + (g.L[d] - 1) * g.stride[d] : s - g.stride[d];
+}
+
 // site reached from coordinates c by n steps along direction d (periodic), without changing c
 __device__ __forceinline__ int shifted(const Geom& g, const int c[4], int d, int n) {
     int s = 0;
@@ -334,11 +347,15 @@ inline int site_blocks(const rmhmc_ctx* ctx) { return (ctx->g.V + kBlock - 1) / 
 // blocks of the stencil kernels: four lanes per site (one per field component mu)
 inline int lane_blocks(const rmhmc_ctx* ctx) { return (int)(((size_t)ctx->g.V * 4 + kBlock - 1) / kBlock); }
 // grids of the reduced kernels hold at most one full wave (2048 threads per SM) and stride over the rest:
-// the deterministic final sum then has at most 16 * SMs block partials
+// the deterministic final sum then has at most 16 * SMs block partials.  Above one wave the grid is trimmed
+// so that every thread strides the same number of times (no tail pass with a partly idle grid, whose blocks
+// would wait at the final reduction)
 inline int capped_grid(const rmhmc_ctx* ctx, size_t threads, int block) {
     const size_t need = (threads + block - 1) / block;
     const size_t cap = (size_t)ctx->num_sms * (2048 / block);
-    return (int)std::max<size_t>(1, std::min(need, cap));
+    if (need <= cap) return (int)std::max<size_t>(1, need);
+    const size_t passes = (need + cap - 1) / cap;
+    return (int)((need + passes - 1) / passes);
 }
 inline Links64 links64(const rmhmc_ctx* ctx) { return Links64{ctx->u64, ctx->g.V}; }
 inline Links32 links32(const rmhmc_ctx* ctx) { return Links32{ctx->u32a, ctx->u32b, ctx->g.V}; }

@@ -538,7 +538,15 @@ static int check_params(rmhmc_ctx* ctx, const rmhmc_params* p) {
         return set_err(ctx, RMHMC_EINVAL, "tolerances and iteration caps must be positive");
     if (p->prec != RMHMC_FP64 && p->prec != RMHMC_MIXED) return set_err(ctx, RMHMC_EINVAL, "bad prec");
     if (p->symplectic != 0 && p->symplectic != 1) return set_err(ctx, RMHMC_EINVAL, "symplectic must be 0 or 1");
+    if (p->fg_fp64 != 0 && p->fg_fp64 != 1) return set_err(ctx, RMHMC_EINVAL, "fg_fp64 must be 0 or 1");
+    if (p->fp_extra < 0 || p->fp_extra >= p->fp_maxit)
+        return set_err(ctx, RMHMC_EINVAL, "fp_extra must lie in [0, fp_maxit)");
     return RMHMC_OK;
+}
+
+// precision of the gauge force inside the MD (the float64 MD is float64 throughout)
+static int md_gauge_prec(const rmhmc_params* p) {
+    return (p->prec == RMHMC_FP64 || p->fg_fp64) ? RMHMC_FP64 : RMHMC_FP32;
 }
 
 // The log|M| term of Eq. (5) through an auxiliary field: phi (fixed in the MD) with action
@@ -568,7 +576,7 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
     RM_TRY(md_work(ctx, w));
     const size_t fs = field_elems(ctx), lb = sizeof(double) * (size_t)ctx->g.V * 72;
     const double eps = p->tau / p->nsteps;
-    const int gprec = p->prec == RMHMC_FP64 ? RMHMC_FP64 : RMHMC_FP32;
+    const int gprec = md_gauge_prec(p);
     int fp_p = 0, fp_u = 0, solves = 0;
     long long kiters = 0;
     double worst = 0.0;
@@ -576,8 +584,10 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
     RM_TRY(potential_force(ctx, p, gprec, lg, w.FG, st));
     RM_TRY(mom_update(ctx, P, 0.5 * eps, w.FG, nullptr, nullptr, w.Q, nullptr, st));   // Q0 = P + eps/2 F_G
     for (int step = 0; step < p->nsteps; step++) {
-        // (1) momentum fixed point at fixed U
+        // (1) momentum fixed point at fixed U; extra: iterations still to run after convergence (-1: not
+        // converged yet)
         bool conv = false;
+        int extra = -1;
         for (int i = 0; i < p->fp_maxit; i++) {
             int it = 0;
             RM_TRY(kinetic_from_krylov(ctx, m, w.Q, p->tol_md, p->maxiter, p->prec, w.FK, w.V0, nullptr, &it, st));
@@ -590,7 +600,9 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
             RM_TRY(read_max(ctx, w.dmax, &d, st));
             fp_p++;
             if (!isfinite(d)) return set_err(ctx, RMHMC_ENAN, "NaN/Inf in the momentum fixed point");
-            if (d <= p->fp_tol) { conv = true; worst = std::max(worst, d); break; }
+            if (extra < 0 && d <= p->fp_tol) { extra = p->fp_extra; worst = std::max(worst, d); }
+            if (extra == 0) { conv = true; break; }
+            if (extra > 0) extra--;
         }
         if (!conv) return set_err(ctx, RMHMC_ENOCONV, "momentum fixed point: no convergence in %d iterations", p->fp_maxit);
         // (2) link fixed point: B = exp(i eps/2 V0) U ; W = exp(i eps V0) U ; W <- exp(i eps/2 V(W)) B.
@@ -604,6 +616,7 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
         if (it32) RM_TRY(link_iter32_launch(ctx, U, w.V0, eps, w.W32, false, nullptr, st));
         else RM_TRY(link_update_launch(ctx, U, w.V0, eps, false, w.W, nullptr, nullptr, true, st));
         conv = false;
+        extra = -1;
         for (int i = 0; i < p->fp_maxit; i++) {
             int it = 0;
             RM_TRY(kinetic_from_krylov(ctx, m, w.Q, p->tol_md, p->maxiter, p->prec, w.FK, w.V0, nullptr, &it, st));
@@ -619,7 +632,9 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
             fp_u++;
             if (!isfinite(d)) return set_err(ctx, RMHMC_ENAN, "NaN/Inf in the link fixed point");
             if (!it32) RM_CHECK(ctx, cudaMemcpyAsync(w.W, U, lb, cudaMemcpyDeviceToDevice, st));
-            if (d <= p->fp_tol) { conv = true; worst = std::max(worst, d); break; }
+            if (extra < 0 && d <= p->fp_tol) { extra = p->fp_extra; worst = std::max(worst, d); }
+            if (extra == 0) { conv = true; break; }
+            if (extra > 0) extra--;
         }
         if (!conv) return set_err(ctx, RMHMC_ENOCONV, "link fixed point: no convergence in %d iterations", p->fp_maxit);
         // the accepted links, reunitarised, with fresh internal copies
@@ -648,14 +663,19 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
 // graph launch with no host round trip.  Status codes written on the device: 1 Krylov cap, 2 Krylov NaN,
 // 3 fixed point without convergence, 4 fixed point NaN.
 // ------------------------------------------------------------------------------------------------
-__global__ void k_fp_decide(double* dmax, int* iter, int cap, double tol, cudaGraphConditionalHandle h, long long* count,
-                            int* status) {
+// iter[0]: iterations of this fixed point; iter[1]: iterations still to run after convergence (-1 before it)
+__global__ void k_fp_decide(double* dmax, int* iter, int cap, double tol, int extra, cudaGraphConditionalHandle h,
+                            long long* count, int* status) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double d = *dmax;
-    const int it = ++(*iter);
+    const int it = ++iter[0];
     (*count)++;
     const bool bad = !(d == d) || isinf(d);
-    const bool done = d <= tol;
+    int rem = iter[1];
+    if (rem < 0 && d <= tol) rem = extra;
+    const bool done = rem == 0;
+    if (rem > 0) rem--;
+    iter[1] = rem;
     if (bad) atomicMax(status, 4);
     else if (!done && it >= cap) atomicMax(status, 3);
     cudaGraphSetConditional(h, (!done && !bad && it < cap) ? 1u : 0u);
@@ -665,7 +685,7 @@ __global__ void k_fp_decide(double* dmax, int* iter, int cap, double tol, cudaGr
 struct MDGraphBufs {
     double *U, *P;               // the trajectory's links and momenta (context-owned copies)
     long long* stats;            // [0] Krylov iterations, [1] momentum fixed-point iterations, [2] link ones
-    int* ints;                   // [0] status, [1] loop iteration counter
+    int* ints;                   // [0] status, [1] loop iteration counter, [2] iterations left after convergence
 };
 
 static int md_graph_bufs(rmhmc_ctx* ctx, MDGraphBufs& b) {
@@ -682,8 +702,8 @@ static int md_graph_bufs(rmhmc_ctx* ctx, MDGraphBufs& b) {
 
 static std::string md_key(const rmhmc_params* p, const MassTerm& m) {
     char buf[512];
-    snprintf(buf, sizeof buf, "%d|%.17g|%.17g|%.17g|%d|%.17g|%.17g|%d|%d|%.17g|%d", p->prec, p->beta, p->c1, p->tau,
-             p->nsteps, p->tol_md, p->fp_tol, p->fp_maxit, p->maxiter, m.c, m.npole());
+    snprintf(buf, sizeof buf, "%d|%.17g|%.17g|%.17g|%d|%.17g|%.17g|%d|%d|%d|%d|%.17g|%d", p->prec, p->beta, p->c1, p->tau,
+             p->nsteps, p->tol_md, p->fp_tol, p->fp_maxit, p->fp_extra, md_gauge_prec(p), p->maxiter, m.c, m.npole());
     std::string k(buf);
     for (int j = 0; j < m.npole(); j++) {
         snprintf(buf, sizeof buf, "|%.17g,%.17g", m.alpha[j], m.sigma[j]);
@@ -696,7 +716,7 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
                             const MDWork& w, const AuxTerm* lg, cudaGraph_t* out) {
     cudaStream_t st = ctx->cap_st[0], aux = ctx->cap_st[1], aux2 = ctx->cap_st[2];
     const double eps = p->tau / p->nsteps;
-    const int gprec = RMHMC_FP32;
+    const int gprec = md_gauge_prec(p);
     RM_CHECK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     int s = RMHMC_OK;
     do {
@@ -715,7 +735,8 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
         for (int step = 0; step < p->nsteps && s == RMHMC_OK; step++) {
             // (1) momentum fixed point
             if (cudaMemsetAsync(w.dmax, 0, sizeof(double), st) != cudaSuccess ||
-                cudaMemsetAsync(gb.ints + 1, 0, sizeof(int), st) != cudaSuccess) { s = RMHMC_ECUDA; break; }
+                cudaMemsetAsync(gb.ints + 1, 0, sizeof(int), st) != cudaSuccess ||
+                cudaMemsetAsync(gb.ints + 2, 0xff, sizeof(int), st) != cudaSuccess) { s = RMHMC_ECUDA; break; }
             cudaGraphConditionalHandle h1;
             cudaGraph_t body;
             if ((s = capture_handle(ctx, st, 1u, &h1)) != RMHMC_OK) break;
@@ -727,7 +748,8 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
             s = kinetic_enqueue(ctx, m, w.Q, p->tol_md, p->maxiter, w.FK, w.V0, gb.stats, gb.ints, aux, aux2);
             if (s == RMHMC_OK) s = mom_update(ctx, gb.P, 0.5 * eps, w.FG, w.FK, w.Q, w.Q, w.dmax, aux);
             if (s == RMHMC_OK) {
-                k_fp_decide<<<1, 32, 0, aux>>>(w.dmax, gb.ints + 1, p->fp_maxit, p->fp_tol, h1, gb.stats + 1, gb.ints);
+                k_fp_decide<<<1, 32, 0, aux>>>(w.dmax, gb.ints + 1, p->fp_maxit, p->fp_tol, p->fp_extra, h1, gb.stats + 1,
+                                                gb.ints);
                 ++ctx->launches;
             }
             {
@@ -742,7 +764,8 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
             else s = link_update_launch(ctx, gb.U, w.V0, eps, false, w.W, nullptr, nullptr, true, st);
             if (s != RMHMC_OK) break;
             if (cudaMemsetAsync(w.dmax, 0, sizeof(double), st) != cudaSuccess ||
-                cudaMemsetAsync(gb.ints + 1, 0, sizeof(int), st) != cudaSuccess) { s = RMHMC_ECUDA; break; }
+                cudaMemsetAsync(gb.ints + 1, 0, sizeof(int), st) != cudaSuccess ||
+                cudaMemsetAsync(gb.ints + 2, 0xff, sizeof(int), st) != cudaSuccess) { s = RMHMC_ECUDA; break; }
             cudaGraphConditionalHandle h2;
             if ((s = capture_handle(ctx, st, 1u, &h2)) != RMHMC_OK) break;
             if ((s = capture_while(ctx, st, h2, &body)) != RMHMC_OK) break;
@@ -759,7 +782,8 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
                     s = RMHMC_ECUDA;
             }
             if (s == RMHMC_OK) {
-                k_fp_decide<<<1, 32, 0, aux>>>(w.dmax, gb.ints + 1, p->fp_maxit, p->fp_tol, h2, gb.stats + 2, gb.ints);
+                k_fp_decide<<<1, 32, 0, aux>>>(w.dmax, gb.ints + 1, p->fp_maxit, p->fp_tol, p->fp_extra, h2, gb.stats + 2,
+                                                gb.ints);
                 ++ctx->launches;
             }
             {

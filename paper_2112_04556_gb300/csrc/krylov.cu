@@ -1169,12 +1169,13 @@ int kinetic_enqueue(rmhmc_ctx* ctx, const MassTerm& m, const double* P, double t
 
 using namespace rm;
 
-extern "C" int rat_mass_solve(rmhmc_ctx* ctx, const double* U, const double* b, int nshift, const double* sigma,
-                              const double* alpha, double c, double tol, int maxiter, int prec, double* y, double* xs,
-                              int* iters, double* resid, cudaStream_t stream) {
+extern "C" int rat_mass_solve(rmhmc_ctx* ctx, const double* U, const double* b, int nfield, int nshift,
+                              const double* sigma, const double* alpha, double c, double tol, int maxiter, int prec,
+                              double* y, double* xs, int* iters, double* resid, cudaStream_t stream) {
     if (!ctx) return RMHMC_EINVAL;
     ctx->err.clear();
-    if (!b || !y) return set_err(ctx, RMHMC_EINVAL, "rat_mass_solve: null field");
+    if (nfield < 0 || nfield > 65535) return set_err(ctx, RMHMC_EINVAL, "rat_mass_solve: nfield in [0, 65535]");
+    if (nfield > 0 && (!b || !y)) return set_err(ctx, RMHMC_EINVAL, "rat_mass_solve: null field");
     if (nshift < 0 || nshift > 24 || (nshift > 0 && (!sigma || !alpha)))
         return set_err(ctx, RMHMC_EINVAL, "rat_mass_solve: bad shifts");
     if (!(tol > 0.0) || maxiter < 1) return set_err(ctx, RMHMC_EINVAL, "rat_mass_solve: bad tolerance or maxiter");
@@ -1185,18 +1186,24 @@ extern "C" int rat_mass_solve(rmhmc_ctx* ctx, const double* U, const double* b, 
     MassTerm m;
     RM_TRY(parse_mass(ctx, &mm, m));
     RM_TRY(ensure_links(ctx, U, stream));
+    if (iters) *iters = 0;
     const size_t fs = field_elems(ctx);
     int status = RMHMC_OK;
-    double* x = xs;
-    if (!x && nshift > 0) {
-        x = (double*)workspace(ctx, "rs_xs", sizeof(double) * fs * nshift, &status);
-        if (!x) return status;
+    double* xw = nullptr;   // shared workspace of the shifted solutions when the caller wants none
+    if (!xs && nshift > 0) {
+        xw = (double*)workspace(ctx, "rs_xs", sizeof(double) * fs * nshift, &status);
+        if (!xw) return status;
     }
-    int it = 0;
-    RM_TRY(solve_shifts(ctx, m, b, tol, maxiter, prec, x, &it, resid, stream));
-    // y = c b + sum_j alpha_j x_j (float64)
-    RM_TRY(axpby64(ctx, c, b, 0.0, nullptr, y, fs, stream));
-    for (int j = 0; j < nshift; j++) RM_TRY(axpby64(ctx, 1.0, y, alpha[j], x + (size_t)j * fs, y, fs, stream));
-    if (iters) *iters = it;
+    for (int f = 0; f < nfield; f++) {
+        const double* bf = b + (size_t)f * fs;
+        double* yf = y + (size_t)f * fs;
+        double* x = xs ? xs + (size_t)f * nshift * fs : xw;
+        int it = 0;
+        RM_TRY(solve_shifts(ctx, m, bf, tol, maxiter, prec, x, &it, resid ? resid + (size_t)f * nshift : nullptr, stream));
+        // y_f = c b_f + sum_j alpha_j x_fj (float64)
+        RM_TRY(axpby64(ctx, c, bf, 0.0, nullptr, yf, fs, stream));
+        for (int j = 0; j < nshift; j++) RM_TRY(axpby64(ctx, 1.0, yf, alpha[j], x + (size_t)j * fs, yf, fs, stream));
+        if (iters) *iters += it;
+    }
     return RMHMC_OK;
 }

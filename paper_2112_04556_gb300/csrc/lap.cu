@@ -173,6 +173,8 @@ int launch_lap(rmhmc_ctx* ctx, int prec, int linkfmt, const void* X, void* Y, in
             return launch_lap_t<double, 12>(ctx, (const double*)X, (double*)Y, nfield, a, b, (const double*)W, c, slot, st);
         return launch_lap_t<double, 18>(ctx, (const double*)X, (double*)Y, nfield, a, b, (const double*)W, c, slot, st);
     }
+    if (nfield >= kAdMinFields)
+        return launch_lap_ad(ctx, linkfmt, (const float*)X, (float*)Y, nfield, a, b, (const float*)W, c, slot, st);
     if (linkfmt == 12)
         return launch_lap_t<float, 12>(ctx, (const float*)X, (float*)Y, nfield, a, b, (const float*)W, c, slot, st);
     return launch_lap_t<float, 18>(ctx, (const float*)X, (float*)Y, nfield, a, b, (const float*)W, c, slot, st);

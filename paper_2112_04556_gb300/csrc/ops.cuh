@@ -9,6 +9,13 @@ namespace rm {
 int launch_lap(rmhmc_ctx* ctx, int prec, int linkfmt, const void* X, void* Y, int nfield, double a, double b,
                const void* W, double c, int slot, cudaStream_t st);
 
+// the same for float32 fields in the adjoint form (lap_ad.cu): each link becomes its 8x8 adjoint matrix once per
+// application, shared by all fields; dots as launch_lap
+int launch_lap_ad(rmhmc_ctx* ctx, int linkfmt, const float* X, float* Y, int nfield, double a, double b, const float* W,
+                  double c, int slot, cudaStream_t st);
+// fewest fields for which launch_lap takes the adjoint form
+constexpr int kAdMinFields = 2;
+
 // gauge force F = -dS/dw (float64 output; arithmetic float64 or float32) from the context's links
 int gauge_force_launch(rmhmc_ctx* ctx, double beta, double c1, int prec, double* F, cudaStream_t st);
 // action S and average plaquette (float64, deterministic) from the context's float64 links

@@ -256,3 +256,64 @@ template <typename T> RM_HD void antiherm_coef(const mat3<T>& M, T* k) {
 }
 
 }  // namespace rm
+
+namespace rm {
+
+// Adjoint matrix of a link: Ad[a][b] = 2 Tr(T^a U T^b U^dag), the real 8x8 orthogonal matrix with
+// (U X U^dag)^a = sum_b Ad[a][b] x^b for X = sum_b x^b T^b (and (U^dag X U)^a = sum_b Ad[b][a] x^b).
+// Built from the columns u_k of U: U lambda^b U^dag is a combination of the outer products
+// p_kl = u_k u_l^dag (lambda^{1,2}: k,l = 0,1; lambda^{4,5}: 0,2; lambda^{6,7}: 1,2; lambda^{3,8}: p_kk),
+// and Ad[a][b] = Tr(lambda^a U lambda^b U^dag) / 2 reads the Hermitian entries of that combination.
+// The columns are handed to sink(b, col) one at a time (col[a] = Ad[a][b]), in the order 0, 1, 3, 4, 5, 6, 2, 7.
+template <typename T, class Sink>
+__device__ __forceinline__ void adjoint_columns(const mat3<T>& U, Sink&& sink) {
+    const T r3 = T(0.57735026918962576451);   // 1/sqrt(3)
+    // column b from the entries 00, 11, 22 (real) and 01, 02, 12 of the Hermitian M = U lambda^b U^dag
+    auto put = [&](int b, T m00, T m11, T m22, cplx<T> m01, cplx<T> m02, cplx<T> m12) {
+        const T col[8] = {m01.re, -m01.im, T(0.5) * (m00 - m11), m02.re, -m02.im, m12.re, -m12.im,
+                          T(0.5) * r3 * (m00 + m11 - T(2) * m22)};
+        sink(b, col);
+    };
+    // (k, l) pairs: S = p + p^dag (lambda^{1,4,6}), D = -i (p - p^dag) (lambda^{2,5,7})
+    constexpr int pk[3] = {0, 0, 1}, pl[3] = {1, 2, 2}, pb[3] = {0, 3, 5};
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        const int k = pk[q], l = pl[q];
+        cplx<T> p[3][3];   // p[i][j] = U_ik conj(U_jl)
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) p[i][j] = cmul(U.e[i][k], cconj(U.e[j][l]));
+        // S_ii = 2 Re p_ii, S_ij = p_ij + conj(p_ji); D_ii = 2 Im p_ii, D_ij = -i (p_ij - conj(p_ji))
+        auto s_off = [&](int i, int j) { return cadd(p[i][j], cconj(p[j][i])); };
+        auto d_off = [&](int i, int j) {
+            const cplx<T> e = csub(p[i][j], cconj(p[j][i]));
+            return cmk(e.im, -e.re);
+        };
+        put(pb[q], T(2) * p[0][0].re, T(2) * p[1][1].re, T(2) * p[2][2].re, s_off(0, 1), s_off(0, 2), s_off(1, 2));
+        put(pb[q] + 1, T(2) * p[0][0].im, T(2) * p[1][1].im, T(2) * p[2][2].im, d_off(0, 1), d_off(0, 2), d_off(1, 2));
+    }
+    // g_k = u_k u_k^dag: lambda^3 -> g_0 - g_1, lambda^8 -> (g_0 + g_1 - 2 g_2)/sqrt(3)
+    T gd[3][3];
+    cplx<T> go[3][3];   // [k][01, 02, 12]
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+#pragma unroll
+        for (int i = 0; i < 3; i++) gd[k][i] = U.e[i][k].re * U.e[i][k].re + U.e[i][k].im * U.e[i][k].im;
+        go[k][0] = cmul(U.e[0][k], cconj(U.e[1][k]));
+        go[k][1] = cmul(U.e[0][k], cconj(U.e[2][k]));
+        go[k][2] = cmul(U.e[1][k], cconj(U.e[2][k]));
+    }
+    put(2, gd[0][0] - gd[1][0], gd[0][1] - gd[1][1], gd[0][2] - gd[1][2], csub(go[0][0], go[1][0]),
+        csub(go[0][1], go[1][1]), csub(go[0][2], go[1][2]));
+    T d8[3];
+    cplx<T> o8[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        d8[i] = r3 * (gd[0][i] + gd[1][i] - T(2) * gd[2][i]);
+        o8[i] = cscale(csub(cadd(go[0][i], go[1][i]), cscale(go[2][i], T(2))), r3);
+    }
+    put(7, d8[0], d8[1], d8[2], o8[0], o8[1], o8[2]);
+}
+
+}  // namespace rm

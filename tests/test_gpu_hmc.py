@@ -139,6 +139,45 @@ def test_mixed_vs_fp64_dH_16_4():
     assert abs(out[1][0]["H0"] - out[0][0]["H0"]) <= 1e-9 * abs(out[0][0]["H0"])
 
 
+def test_fp_extra_iterations_graph_and_host():
+    """fp_extra: each fixed point runs exactly fp_extra iterations past its first convergence (the iterates are
+    deterministic, so the counts add 2 x fp_extra per step), the graph and host-driven MD agree bit for bit with
+    and without it and with the float64 gauge force, and the extra iterations bring the mixed trajectory closer
+    to the oracle's converged float64 one."""
+    import paper_2112_04556_gb300 as rm
+    L = (6, 4, 4, 8)
+    U = inputs.random_links(L, eps=0.3, seed=71)
+    m = fit.mass_term(12, 0.9)
+    xi = oracle.gauss_field(L, 3, 0, 0)
+    ref = oracle.trajectory(L, U, xi, oracle.uniform(3, 0), 0.3, 3, 6.0, 0.0, m, tol_md=1e-13, tol_h=1e-13,
+                            fp_tol=1e-13, metropolis=False)
+    out = {}
+    with rm.Context(L) as ctx:
+        for extra in (0, 2):
+            for fg in (False, True):
+                for graphs in (True, False):
+                    rm.set_graphs(ctx, graphs)
+                    Ud = dev(U)
+                    r = rm.rmhmc_trajectory(ctx, Ud, _params(rm, m, tau=0.3, nsteps=3, prec=rm.MIXED, tol_md=1e-6,
+                                                             tol_h=1e-12, fp_tol=1e-6, fp_extra=extra, fg_fp64=fg,
+                                                             metropolis=False))
+                    out[(extra, fg, graphs)] = (r, host(Ud))
+        rm.set_graphs(ctx, True)
+        with pytest.raises(rm.RmhmcError):
+            rm.rmhmc_trajectory(ctx, dev(U), _params(rm, m, prec=rm.MIXED, fp_extra=100, fp_maxit=100))
+    for extra in (0, 2):
+        for fg in (False, True):
+            a, b = out[(extra, fg, True)], out[(extra, fg, False)]
+            assert a[0]["dH"] == b[0]["dH"] and np.array_equal(a[1], b[1])
+            assert a[0]["fp_iters_p"] == b[0]["fp_iters_p"] and a[0]["fp_iters_u"] == b[0]["fp_iters_u"]
+    for fg in (False, True):
+        r0, r2 = out[(0, fg, True)][0], out[(2, fg, True)][0]
+        assert r2["fp_iters_p"] == r0["fp_iters_p"] + 2 * 3 and r2["fp_iters_u"] == r0["fp_iters_u"] + 2 * 3
+    for key in out:
+        assert np.abs(out[key][1] - ref["U1"]).max() < 2e-6, key
+        assert abs(out[key][0]["dH"] - ref["dH"]) < 1e-4, key
+
+
 def test_trajectory_errors_leave_links_unchanged():
     import paper_2112_04556_gb300 as rm
     L = (4, 4, 4, 4)

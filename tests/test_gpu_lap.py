@@ -21,10 +21,12 @@ def _run(ctx, U_d, X, prec, linkfmt, op=0):
 
 @pytest.mark.parametrize("L", [(4, 4, 4, 4), (2, 4, 6, 8), (5, 3, 4, 7), (3, 3, 3, 3)])
 def test_lap_parity_small(L):
-    """Several 128-site tiles and a ragged last tile (5x3x4x7 = 420 sites); odd extents included."""
+    """Several 128-site tiles and a ragged last tile (5x3x4x7 = 420 sites); odd extents included.  Five
+    fields: the float32 paths take the multi-field adjoint form (tiles of 32 sites, fields in passes of 3,
+    so the last pass is ragged too)."""
     import paper_2112_04556_gb300 as rm
     U = inputs.random_links(L, eps=0.7, seed=1)
-    X = inputs.gaussian_fields(L, 3, seed=2)
+    X = inputs.gaussian_fields(L, 5, seed=2)
     ref = oracle.lap(L, U, X)
     with rm.Context(L) as ctx:
         Ud = dev(U)
@@ -98,3 +100,27 @@ def test_lap_errors_and_empty():
             rm.lap_apply(ctx, None, X[0], linkfmt=9)
         code = rm.lib().lap_apply(ctx.h, None, rm._ptr(X), rm._ptr(X[1]), 0, 0, 18, 0, rm._stream())
         assert code == rm.OK                          # nothing to do for zero fields
+
+
+@pytest.mark.parametrize("nf", [2, 4])
+def test_lap_multifield_full_size_sampled(nf):
+    """32^4, several float32 fields in one launch (the adjoint form), 18- and 12-real links, on sampled sites
+    of every field; each field also equals its own single-field application to float32 rounding."""
+    import paper_2112_04556_gb300 as rm
+    torch = torch_cuda()
+    L = (32, 32, 32, 32)
+    U = inputs.random_links(L, eps=0.3, seed=0)
+    X = inputs.gaussian_fields(L, nf, seed=6)
+    rng = np.random.default_rng(7)
+    V = int(np.prod(L))
+    sites = np.unique(np.concatenate([rng.integers(0, V, 3000), [0, V - 1], np.arange(V - 40, V)]))
+    refs = [oracle.lap_sites(L, U, X[f], sites) for f in range(nf)]
+    with rm.Context(L) as ctx:
+        Ud = dev(U)
+        X32 = dev(X, torch.float32)
+        for lf in (18, 12):
+            Y = host(rm.lap_apply(ctx, Ud, X32, prec=rm.FP32, linkfmt=lf)).astype(np.float64)
+            for f in range(nf):
+                assert rel_l2(Y[f][sites], refs[f]) <= 1e-5, (lf, f)
+            Y1 = host(rm.lap_apply(ctx, None, X32[nf - 1].contiguous(), prec=rm.FP32, linkfmt=lf)).astype(np.float64)
+            assert rel_l2(Y[nf - 1], Y1) <= 2e-6

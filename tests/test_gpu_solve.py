@@ -27,6 +27,28 @@ def test_rat_mass_solve_parity(L, prec, tol, bound):
         assert iters > 0
 
 
+@pytest.mark.parametrize("prec,tol,bound", [(0, 1e-12, 1e-11), (1, 1e-11, 1e-10)])
+def test_rat_mass_solve_nfield(prec, tol, bound):
+    """Three fields in one call (Sec. 3, Eq. 6 applied field by field): every y_f, every x_fj and the
+    per-field residuals against the oracle's per-field rational_apply; iterations add up over fields."""
+    import paper_2112_04556_gb300 as rm
+    L = (5, 3, 4, 7)
+    U = inputs.random_links(L, eps=0.5, seed=25)
+    b = inputs.gaussian_fields(L, 3, seed=26)
+    b[1] *= 1e-3                                # a small field: tol is relative to each field's own norm
+    m = fit.mass_term(12, 0.9)
+    with rm.Context(L) as ctx:
+        y, xs, iters, resid = rm.rat_mass_solve(ctx, dev(U), dev(b), m, tol=tol, prec=prec, want_xs=True)
+        assert resid.shape == (3, 12) and np.all(resid <= tol), resid
+        single = [rm.rat_mass_solve(ctx, None, dev(b[f]), m, tol=tol, prec=prec)[2] for f in range(3)]
+    assert iters == sum(single)
+    for f in range(3):
+        y_ref, xs_ref = oracle.rational_apply(L, U, b[f], m, tol=1e-14)
+        assert rel_l2(host(y[f]), y_ref) <= bound, f
+        for j in range(12):
+            assert rel_l2(host(xs[f, j]), xs_ref[j]) <= 10 * bound, (f, j)
+
+
 def test_single_shift_is_plain_cg():
     import paper_2112_04556_gb300 as rm
     L = (4, 4, 4, 6)
