@@ -12,9 +12,12 @@ needed between steps.
 
 Besides the timed steps the line carries: the roofline of the CG stencil (CUDA events around its
 launches in the host-driven solves; DRAM traffic from an ncu capture of the same launch shape), the
-same steps through host buffers (e2e), one float64 and one mixed trajectory from the same links and
-momenta at tau = 1 and at tau = 0.1 with tight mixed tolerances (fp64_compare), SM clocks sampled
-during the timed region, and the float64 CPU oracle on a bounded sample (cpu_baseline).
+lap_apply block (float32 18/12-real, float64, four fields in one launch; 32^4 and 24^3 x 48), the
+split of a step into trajectory and spectrum, the same steps through host buffers (e2e), float64
+and mixed trajectories from the same links and momenta at the workload's 20 steps and at the
+accepting 40 steps (fp64_compare), three Metropolis trajectories at 40 steps (accepting), SM
+clocks sampled during the timed region, and the float64 CPU oracle on a bounded sample
+(cpu_baseline).
 
 Prints one JSON line (rank 0).  --impl reference times the float64 CPU oracle instead.
 """
@@ -49,9 +52,12 @@ MIXED_FP_TOL = 1e-6
 MIXED_FP_EXTRA = 3
 FP64_TOL = 1e-10
 DH_BAR = 1e-3
-# step count of the accepting setting at 32^4 (tau = 1): <dH> = 200 at 20 steps and falls as eps^4 (the spread
-# of dH across trajectories, ~20, obeys <dH> = sigma^2/2), so 80 steps give <dH> ~ 0.8, acceptance ~ 0.5
-ACCEPT_NSTEPS = 80
+# step counts at 32^4 (tau = 1) beyond the workload's 20: at 20 steps (eps = 0.05) the leapfrog is near its
+# stability edge for this mass term (dH ~ 200, every trajectory rejected); at 40 steps dH ranges from 0.1 to ~20
+# over momentum draws (the float64-vs-mixed comparison at fixed dH runs there, PAIR_NSTEPS), and the accepting
+# setting's trajectories use 64 steps
+PAIR_NSTEPS = 40
+ACCEPT_NSTEPS = 64
 # DRAM bytes (read + write) of one k_cg_A<float,18> launch at 32^4 with k > 0, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_cg_A_fp32_32x32x32x32.md), per tuned launch shape
 # (components per lane, threads per block); a shape without a capture reports null
@@ -179,22 +185,30 @@ def workload_config(nsteps, world):
 
 
 def run_reference(args, rank, world):
+    """The float64 CPU oracle as the reference arm.  Each step is one bounded sample (the oracle_sample work, about
+    10 s); ms_per_step is that sample's measured time, and value = the fraction of a 32^4 step the sample covers
+    divided by that time, i.e. 32^4 steps per second at the oracle's measured per-operation costs."""
     if rank != 0:
         return 0
     s0 = time.perf_counter()
-    vals = []
-    md_solves = 161   # kinetic evaluations of one 20-step trajectory (the GPU runs measure 81 + 80)
+    md_solves = md_solves_estimate(args.nsteps)
+    secs, trajs = [], []
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         s = oracle_sample()
         if i >= args.warmup:
-            vals.append(oracle_traj_seconds(s, md_solves))
-    sec = sum(vals) / len(vals)
-    value = 1.0 / sec
-    sample = ("oracle kinetic-force evaluation + Laplacian at 8^4 per step, scaled by V(32^4)/V(8^4)=256 and "
-              "by %d kinetic evaluations + 3 (heatbath, 2 Hamiltonians) + 1800 spectrum applications" % md_solves)
+            secs.append(time.perf_counter() - t0)
+            trajs.append(oracle_traj_seconds(s, md_solves))
+    sec_step = sum(secs) / len(secs)
+    traj_sec = sum(trajs) / len(trajs)
+    value = 1.0 / traj_sec
+    units = sec_step / traj_sec
+    sample = ("oracle kinetic-force evaluations + Laplacians at 8^4 per step (%.1f s), a fraction %.3g of one 32^4 "
+              "step: V(32^4)/V(8^4) = 256 x (%d kinetic evaluations + 3 for heatbath and Hamiltonians + 1800 "
+              "spectrum applications)" % (sec_step, units, md_solves))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "traj/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_step * 1e3, "units_per_step": units,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.nsteps, world),
             "cpu_baseline": {"value": value, "unit": "traj/s", "cores": s["cores"], "kind": "oracle",
                              "sample": sample},
@@ -202,6 +216,13 @@ def run_reference(args, rank, world):
             "wall_s": time.perf_counter() - s0}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def md_solves_estimate(nsteps):
+    """Kinetic evaluations of one trajectory at the headline settings: 4 fixed-point iterations to the tolerance
+    plus MIXED_FP_EXTRA, for each of the two fixed points of every step, and the first force (the GPU runs count
+    these; at 20 steps 141 + 140)."""
+    return 2 * nsteps * (4 + MIXED_FP_EXTRA) + 1
 
 
 # algorithmic bytes per site of lap_apply: links once (4 x 18 or 12 reals) + every field read once and written
@@ -221,8 +242,8 @@ def lap_fma_per_site(form, nf, linkfmt=18):
 
 def lap_block(rm, torch, inputs, dims, ctx=None, U=None, reps=20):
     """lap_apply timed with CUDA events on the launching stream (warm-up 3, then reps calls): float32 with 18-
-    and 12-real links, float64, and four float32 fields in one launch (the adjoint form).  The inputs (links
-    and fields) are larger than L2 at these sizes, so no flush is needed between calls."""
+    and 12-real links, float64, and the 18 float32 fields of the spectrum in one launch (the adjoint form).  The
+    inputs (links and fields) are larger than L2 at these sizes, so no flush is needed between calls."""
     import numpy as np
     V = int(np.prod(dims))
     own = ctx is None
@@ -232,14 +253,14 @@ def lap_block(rm, torch, inputs, dims, ctx=None, U=None, reps=20):
     rm.set_links(ctx, U)
     X64 = torch.from_numpy(inputs.gaussian_fields(dims, 1, seed=1)[0]).cuda()
     X32 = X64.float()
-    X4 = torch.from_numpy(inputs.gaussian_fields(dims, 4, seed=2)).cuda().float()
+    XM = torch.randn((18,) + tuple(X64.shape), dtype=torch.float32, device=X64.device)
     peak, kind = measured_peaks()
     out = {"lattice": "x".join(map(str, dims)), "peak_gbs": peak, "peak_kind": kind, "fp32_fma_peak_tfma_s": FP32_FMA_PEAK,
            "l2": "inputs larger than L2, no flush", "variants": []}
     st = torch.cuda.current_stream()
     for name, X, prec, lf, nf, form in [("fp32_18", X32, rm.FP32, 18, 1, "3x3"), ("fp32_12", X32, rm.FP32, 12, 1, "3x3"),
                                         ("fp64_18", X64, rm.FP64, 18, 1, "3x3"),
-                                        ("fp32_18_x4", X4, rm.FP32, 18, 4, "adjoint")]:
+                                        ("fp32_18_x18", XM, rm.FP32, 18, 18, "adjoint")]:
         Y = torch.empty_like(X)
         for _ in range(3):
             rm.lap_apply(ctx, None, X, Y, prec=prec, linkfmt=lf)
@@ -285,8 +306,19 @@ def run_kernel(args):
     X32 = X.float()
     Y32 = torch.empty_like(X32)
     mass = rm.mass_fit(NPOLE, KAPPA)
+    if args.shape:
+        nmu, block = (int(v) for v in args.shape.split(","))
+        rm.set_stencil_shape(lat, rm.SHAPE_LAP, rm.FP32, 18, nmu, block)
+        rm.set_stencil_shape(lat, rm.SHAPE_CG, rm.FP32, 18, nmu, block)
+    nf = 1
     if args.kernel == "lap":
         op = lambda: rm.lap_apply(lat, None, X32, Y32, prec=rm.FP32, linkfmt=18)
+    elif args.kernel == "lapmulti":
+        # the 18 fields of the spectrum in one launch (the adjoint form)
+        nf = 18
+        XM = torch.randn((nf,) + tuple(X32.shape), dtype=torch.float32, device="cuda")
+        YM = torch.empty_like(XM)
+        op = lambda: rm.lap_apply(lat, None, XM, YM, prec=rm.FP32, linkfmt=18)
     else:
         op = lambda: rm.kinetic_force(lat, None, X, mass, tol=1e-6, prec=rm.MIXED)
     for _ in range(args.warmup):
@@ -305,8 +337,8 @@ def run_kernel(args):
     cnt = rm.counters(lat)
     peak, kind = measured_peaks()
     line = {"kernel": args.kernel, "lattice": "x".join(map(str, DIMS)), "ms_per_call": ms, "autotune": rm.tuning(lat)}
-    if args.kernel == "lap":
-        line["gbs_alg"] = 544.0 * V / (ms * 1e-3) / 1e9
+    if args.kernel in ("lap", "lapmulti"):
+        line["gbs_alg"] = lap_bytes_per_site(4, 18, nf) * V / (ms * 1e-3) / 1e9
         line["frac_hbm"] = line["gbs_alg"] / peak
     else:
         avg = cnt["cg_ms"] / max(cnt["cg_count"], 1)
@@ -319,8 +351,10 @@ def run_kernel(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["lap", "cg"], default=None,
+    ap.add_argument("--kernel", choices=["lap", "cg", "lapmulti"], default=None,
                     help="time one kernel family instead of the workload (for profiling)")
+    ap.add_argument("--shape", default=None,
+                    help="pin the float32 stencil shape of --kernel lap/cg as nmu,block (8,256: the link-centric kernel)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
@@ -333,7 +367,6 @@ def main():
     ap.add_argument("--therm", type=int, default=20, help="plain-HMC thermalisation trajectories")
     ap.add_argument("--graphs", choices=["on", "off"], default="on",
                     help="run the mixed-precision MD as one CUDA graph per trajectory")
-    ap.add_argument("--no-parity", action="store_true", help="skip the small-step float64-vs-mixed dH parity pair")
     ap.add_argument("--no-lap", action="store_true", help="skip the lap_apply block")
     ap.add_argument("--no-accept", action="store_true", help="skip the accepting-setting trajectories")
     ap.add_argument("--compare-tau", type=float, default=TAU,
@@ -493,38 +526,38 @@ def main():
         r["seconds"] = time.perf_counter() - t0
         return r
 
-    # mixed vs float64 at fixed dH: both from the same links and momenta, the headline's settings
+    def pair(tau, nsteps, idx):
+        """one float64 and one mixed trajectory (the headline's mixed settings) from the same links and momenta"""
+        ra = timed_traj(U_start.clone(), params(idx, rm.FP64, tau, nsteps))
+        rb = timed_traj(U_start.clone(), params(idx, rm.MIXED, tau, nsteps))
+        d = abs(ra["dH"] - rb["dH"])
+        return {"tau": tau, "nsteps": nsteps, "dH_fp64": ra["dH"], "dH_mixed": rb["dH"], "abs_dH_diff": d,
+                "meets_dH_bar": bool(d <= DH_BAR), "accepted_fp64": ra["accepted"], "accepted_mixed": rb["accepted"],
+                "seconds_fp64": ra["seconds"], "seconds_mixed": rb["seconds"],
+                "traj_per_s_fp64": 1.0 / ra["seconds"], "traj_per_s_mixed": 1.0 / rb["seconds"],
+                "speedup_mixed_over_fp64": ra["seconds"] / rb["seconds"], "plaq_fp64": ra["plaq"],
+                "plaq_mixed": rb["plaq"], "md_iters_fp64": ra["md_iters"], "md_iters_mixed": rb["md_iters"],
+                "fp_iters_fp64": [ra["fp_iters_p"], ra["fp_iters_u"]],
+                "fp_iters_mixed": [rb["fp_iters_p"], rb["fp_iters_u"]]}
+
+    # mixed vs float64 at fixed dH: at the workload's 20 steps and at 40 steps (tau = 1 both)
     fp64 = None
     if world == 1 and not args.no_fp64:
-        ra = timed_traj(U_start.clone(), params(0, rm.FP64, args.compare_tau))
-        rb = timed_traj(U_start.clone(), params(0, rm.MIXED, args.compare_tau))
-        d = abs(ra["dH"] - rb["dH"])
-        fp64 = {"tau": args.compare_tau, "nsteps": args.nsteps,
-                "mixed": {"tol_md": MIXED_TOL_MD, "fp_tol": MIXED_FP_TOL, "fp_extra": MIXED_FP_EXTRA},
+        fp64 = {"dH_bar": DH_BAR, "mixed": {"tol_md": MIXED_TOL_MD, "fp_tol": MIXED_FP_TOL, "fp_extra": MIXED_FP_EXTRA},
                 "fp64": {"tol_md": FP64_TOL, "fp_tol": FP64_TOL},
-                "traj_per_s_fp64": 1.0 / ra["seconds"], "seconds_fp64": ra["seconds"], "seconds_mixed": rb["seconds"],
-                "speedup_mixed_over_fp64": ra["seconds"] / rb["seconds"],
-                "dH_fp64": ra["dH"], "dH_mixed": rb["dH"], "abs_dH_diff": d, "dH_bar": DH_BAR,
-                "meets_dH_bar": bool(d <= DH_BAR), "plaq_fp64": ra["plaq"], "plaq_mixed": rb["plaq"],
-                "md_iters_fp64": ra["md_iters"], "md_iters_mixed": rb["md_iters"],
-                "fp_iters_fp64": [ra["fp_iters_p"], ra["fp_iters_u"]], "fp_iters_mixed": [rb["fp_iters_p"], rb["fp_iters_u"]]}
-        # the same pair where dH = O(0.1): tau = 0.1 in the same 20 steps
-        if not args.no_parity:
-            ra = timed_traj(U_start.clone(), params(0, rm.FP64, 0.1, metropolis=False))
-            rb = timed_traj(U_start.clone(), params(0, rm.MIXED, 0.1, metropolis=False))
-            fp64["small_step"] = {"tau": 0.1, "nsteps": args.nsteps, "dH_fp64": ra["dH"], "dH_mixed": rb["dH"],
-                                  "abs_dH_diff": abs(ra["dH"] - rb["dH"]), "seconds_fp64": ra["seconds"],
-                                  "seconds_mixed": rb["seconds"], "speedup_mixed_over_fp64": ra["seconds"] / rb["seconds"]}
+                "workload_steps": pair(args.compare_tau, args.nsteps, 0)}
+        if not args.no_accept:
+            fp64["stable_steps"] = pair(args.compare_tau, PAIR_NSTEPS, 0)
 
-    # an accepting setting at 32^4: tau = 1 in ACCEPT_NSTEPS steps (mixed, the headline's tolerances), from the
-    # same start, two trajectories with Metropolis
+    # the accepting setting at 32^4 (tau = 1 in ACCEPT_NSTEPS steps, the headline's mixed tolerances): three
+    # consecutive trajectories with Metropolis from the thermalised start
     accept = None
     if rank == 0 and not args.no_accept:
         Ua = U_start.clone()
-        runs = [timed_traj(Ua, params(20000 + i, rm.MIXED, TAU, ACCEPT_NSTEPS)) for i in range(2)]
+        runs = [timed_traj(Ua, params(20000 + i, rm.MIXED, TAU, ACCEPT_NSTEPS)) for i in range(3)]
         accept = {"tau": TAU, "nsteps": ACCEPT_NSTEPS, "dH": [r["dH"] for r in runs],
                   "accepted": [r["accepted"] for r in runs], "seconds": [r["seconds"] for r in runs],
-                  "traj_per_s": 2.0 / sum(r["seconds"] for r in runs),
+                  "traj_per_s": len(runs) / sum(r["seconds"] for r in runs),
                   "acceptance_expected": [min(1.0, math.exp(-r["dH"])) for r in runs]}
 
     if rank != 0:

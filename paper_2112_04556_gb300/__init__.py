@@ -95,6 +95,7 @@ def lib():
         "rmhmc_set_profiling": ([P, I], I),
         "rmhmc_tuning": ([P, ctypes.c_char_p, I], I),
         "rmhmc_set_graphs": ([P, I], I),
+        "rmhmc_set_stencil_shape": ([P, I, I, I, I, I], I),
         "wilson_flow": ([P, P, D, I, I, DP, P], I),
         "cheb_window_coeffs": ([I, DP, I, I, DP], I),
         "rmhmc_mass_fit_spectrum": ([I, DP, DP, I, D, D, DP, DP, DP, DP], I),
@@ -197,6 +198,14 @@ def counters(ctx, reset=False):
 def set_graphs(ctx, on=True):
     """Run the mixed-precision MD as one CUDA graph (default) or host-driven."""
     ctx.check(lib().rmhmc_set_graphs(ctx.h, int(bool(on))))
+
+
+SHAPE_LAP, SHAPE_CG = 0, 1
+
+
+def set_stencil_shape(ctx, kernel, prec, linkfmt, nmu, block):
+    """Pin a stencil launch shape (see rmhmc_set_stencil_shape); nmu = 8 is the link-centric kernel."""
+    ctx.check(lib().rmhmc_set_stencil_shape(ctx.h, int(kernel), int(prec), int(linkfmt), int(nmu), int(block)))
 
 
 def tuning(ctx):

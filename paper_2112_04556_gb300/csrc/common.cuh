@@ -355,7 +355,9 @@ inline int capped_grid(const rmhmc_ctx* ctx, size_t threads, int block) {
     const size_t cap = (size_t)ctx->num_sms * (2048 / block);
     if (need <= cap) return (int)std::max<size_t>(1, need);
     const size_t passes = (need + cap - 1) / cap;
-    return (int)((need + passes - 1) / passes);
+    const size_t sms = std::max<size_t>(1, ctx->num_sms);
+    const size_t g = (need + passes - 1) / passes;
+    return (int)std::min(cap, (g + sms - 1) / sms * sms);   // whole blocks per SM
 }
 inline Links64 links64(const rmhmc_ctx* ctx) { return Links64{ctx->u64, ctx->g.V}; }
 inline Links32 links32(const rmhmc_ctx* ctx) { return Links32{ctx->u32a, ctx->u32b, ctx->g.V}; }

@@ -225,6 +225,27 @@ extern "C" int rmhmc_tuning(const rmhmc_ctx* ctx, char* buf, int len) {
     return RMHMC_OK;
 }
 
+extern "C" int rmhmc_set_stencil_shape(rmhmc_ctx* ctx, int kernel, int prec, int linkfmt, int nmu, int block) {
+    if (!ctx) return RMHMC_EINVAL;
+    ctx->err.clear();
+    if (kernel != RMHMC_SHAPE_LAP && kernel != RMHMC_SHAPE_CG) return set_err(ctx, RMHMC_EINVAL, "bad kernel");
+    if (prec != RMHMC_FP64 && prec != RMHMC_FP32) return set_err(ctx, RMHMC_EINVAL, "bad prec");
+    if (linkfmt != 18 && (linkfmt != 12 || kernel == RMHMC_SHAPE_CG)) return set_err(ctx, RMHMC_EINVAL, "bad linkfmt");
+    if (nmu != 0 && nmu != 1 && nmu != 2 && nmu != 4 && nmu != 8) return set_err(ctx, RMHMC_EINVAL, "bad nmu");
+    if (block != 64 && block != 128 && block != 256) return set_err(ctx, RMHMC_EINVAL, "bad block");
+    if (nmu == 8 && (prec != RMHMC_FP32 || block != 256))
+        return set_err(ctx, RMHMC_EINVAL, "the link-centric kernel is float32 with 256 threads");
+    const int bytes = prec == RMHMC_FP64 ? 8 : 4;
+    const int key = (kernel == RMHMC_SHAPE_CG ? 10000 : 0) + bytes * 100 + linkfmt;
+    if (kernel == RMHMC_SHAPE_CG && !ctx->tune.count(bytes * 100 + 18)) ctx->tune[bytes * 100 + 18] = {2, 256};
+    ctx->tune[key] = {nmu, block};
+    char line[96];
+    snprintf(line, sizeof line, "%s%s %s LF%d pinned -> nmu %d block %d", ctx->tune_report.empty() ? "" : "; ",
+             kernel == RMHMC_SHAPE_CG ? "cg" : "lap", bytes == 8 ? "fp64" : "fp32", linkfmt, nmu, block);
+    ctx->tune_report += line;
+    return RMHMC_OK;
+}
+
 extern "C" int rmhmc_set_graphs(rmhmc_ctx* ctx, int on) {
     if (!ctx) return RMHMC_EINVAL;
     ctx->use_graphs = on != 0;

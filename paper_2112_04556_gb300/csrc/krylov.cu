@@ -138,6 +138,22 @@ static void launch_cg_A(rmhmc_ctx* ctx, const StencilShape& shp, typename LinksO
     ++ctx->launches;
 }
 
+// the CG stencil in a tuned shape: 3x3 gather kernels (nmu 1, 2, 4, 0) or, in float32, the link-centric
+// adjoint kernel (nmu 8, lap_lc.cu)
+template <typename T>
+static int cg_stencil(rmhmc_ctx* ctx, const StencilShape& shp, typename LinksOf<T>::type U, T* R, size_t fs, T* q, T diag,
+                      int* flags, double* vals, int maxit, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (shp.nmu == 8)
+            return launch_cg_lc(ctx, R, q, diag, flags, vals, maxit, red_slot_partials(ctx, 0), red_slot_counter(ctx, 0), st);
+    }
+    if (shp.nmu == 4) launch_cg_A<T, 4>(ctx, shp, U, R, fs, q, diag, flags, vals, maxit, st);
+    else if (shp.nmu == 2) launch_cg_A<T, 2>(ctx, shp, U, R, fs, q, diag, flags, vals, maxit, st);
+    else if (shp.nmu == 0) launch_cg_A<T, 0>(ctx, shp, U, R, fs, q, diag, flags, vals, maxit, st);
+    else launch_cg_A<T, 1>(ctx, shp, U, R, fs, q, diag, flags, vals, maxit, st);
+    return RMHMC_OK;
+}
+
 // Launch shape of the CG stencil, tuned on its own (its loads differ from the plain stencil's: it also reads
 // and writes q, and the one-component shape reads the basis with 256-bit loads): every shape is timed on the
 // context's lattice (k = 0 on zeroed scratch, three repetitions after a warm-up) at first use.
@@ -171,18 +187,14 @@ static int cg_shape(rmhmc_ctx* ctx, cudaStream_t st, StencilShape& out) {
     StencilShape bs;
     char line[128];
     std::string rep;
-    for (int nmu : {1, 2, 4, 0})
+    for (int nmu : {1, 2, 4, 0, 8})
         for (int block : {64, 128, 256}) {
+            if (nmu == 8 && (sizeof(T) == 8 || block != 256)) continue;   // the link-centric kernel: float32, 256
             const StencilShape shp{nmu, block};
-            auto run = [&]() {
-                if (nmu == 4) launch_cg_A<T, 4>(ctx, shp, U, X, fs, Y, T(1), flags, vals, 1, st);
-                else if (nmu == 2) launch_cg_A<T, 2>(ctx, shp, U, X, fs, Y, T(1), flags, vals, 1, st);
-                else if (nmu == 0) launch_cg_A<T, 0>(ctx, shp, U, X, fs, Y, T(1), flags, vals, 1, st);
-                else launch_cg_A<T, 1>(ctx, shp, U, X, fs, Y, T(1), flags, vals, 1, st);
-            };
-            run();
+            auto run = [&]() { return cg_stencil<T>(ctx, shp, U, X, fs, Y, T(1), flags, vals, 1, st); };
+            RM_TRY(run());
             RM_CHECK(ctx, cudaEventRecord(e0, st));
-            for (int r = 0; r < 3; r++) run();
+            for (int r = 0; r < 3; r++) RM_TRY(run());
             RM_CHECK(ctx, cudaEventRecord(e1, st));
             RM_CHECK(ctx, cudaEventSynchronize(e1));
             RM_LAUNCH_CHECK(ctx);
@@ -529,10 +541,7 @@ int krylov_run(rmhmc_ctx* ctx, const T* b, double sigma0, double tol, int maxit,
             const bool timed = ctx->prof && k < kProfEvents;
             if (timed) RM_CHECK(ctx, cudaEventRecord(ctx->prof_ev[2 * k], st));
             // the solver streams 18-real links, in the tuned launch shape
-            if (shp.nmu == 4) launch_cg_A<T, 4>(ctx, shp, U, R, fs, (T*)w.q, diag, w.flags, w.vals, maxit, st);
-            else if (shp.nmu == 2) launch_cg_A<T, 2>(ctx, shp, U, R, fs, (T*)w.q, diag, w.flags, w.vals, maxit, st);
-            else if (shp.nmu == 0) launch_cg_A<T, 0>(ctx, shp, U, R, fs, (T*)w.q, diag, w.flags, w.vals, maxit, st);
-            else launch_cg_A<T, 1>(ctx, shp, U, R, fs, (T*)w.q, diag, w.flags, w.vals, maxit, st);
+            RM_TRY(cg_stencil<T>(ctx, shp, U, R, fs, (T*)w.q, diag, w.flags, w.vals, maxit, st));
             if (timed) RM_CHECK(ctx, cudaEventRecord(ctx->prof_ev[2 * k + 1], st));
             k_cg_B<T><<<nb, kBlock, 0, st>>>(R, fs, (const T*)w.q, nvec, w.flags, w.vals, maxit, tol2,
                                              red_slot_partials(ctx, kSlotRho), red_slot_counter(ctx, kSlotRho)); ++ctx->launches;
@@ -1143,10 +1152,12 @@ int kinetic_enqueue(rmhmc_ctx* ctx, const MassTerm& m, const double* P, double t
         RM_CHECK(ctx, cudaStreamBeginCaptureToGraph(aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
         const Links32 U = links32(ctx);
         const float diag = (float)(0.5 + s0);
-        if (shp.nmu == 4) launch_cg_A<float, 4>(ctx, shp, U, b.R, fs, b.q, diag, b.flags, b.vals, b.maxit, aux);
-        else if (shp.nmu == 2) launch_cg_A<float, 2>(ctx, shp, U, b.R, fs, b.q, diag, b.flags, b.vals, b.maxit, aux);
-        else if (shp.nmu == 0) launch_cg_A<float, 0>(ctx, shp, U, b.R, fs, b.q, diag, b.flags, b.vals, b.maxit, aux);
-        else launch_cg_A<float, 1>(ctx, shp, U, b.R, fs, b.q, diag, b.flags, b.vals, b.maxit, aux);
+        const int cs = cg_stencil<float>(ctx, shp, U, b.R, fs, b.q, diag, b.flags, b.vals, b.maxit, aux);
+        if (cs != RMHMC_OK) {
+            cudaGraph_t tmp;
+            cudaStreamEndCapture(aux, &tmp);
+            return cs;
+        }
         k_cgg_B<float><<<nb, kBlock, 0, aux>>>(b.R, fs, b.q, nvec, b.flags, b.vals, b.maxit, tol * tol,
                                                red_slot_partials(ctx, kSlotRho), red_slot_counter(ctx, kSlotRho), h,
                                                stats); ++ctx->launches;

@@ -95,6 +95,12 @@ static int launch_lap_t(rmhmc_ctx* ctx, const T* X, T* Y, int nfield, double a, 
                         int slot, cudaStream_t st) {
     StencilShape shp;
     RM_TRY((stencil_shape<T, LF>(ctx, st, shp)));
+    if (shp.nmu == 8) {
+        // the link-centric kernel serves one plain field; with a third term or dots the gather kernel runs
+        if (sizeof(T) == 4 && nfield == 1 && !W && slot < 0)
+            return launch_lap_lc(ctx, LF, (const float*)X, (float*)Y, a, b, st);
+        shp = StencilShape{2, 256};
+    }
     if (shp.nmu == 4) launch_lap_shape<T, LF, 4>(ctx, shp, X, Y, nfield, a, b, W, c, slot, st);
     else if (shp.nmu == 2) launch_lap_shape<T, LF, 2>(ctx, shp, X, Y, nfield, a, b, W, c, slot, st);
     else if (shp.nmu == 0) launch_lap_shape<T, LF, 0>(ctx, shp, X, Y, nfield, a, b, W, c, slot, st);
@@ -128,11 +134,13 @@ int stencil_shape(rmhmc_ctx* ctx, cudaStream_t st, StencilShape& out) {
     StencilShape bs;
     char line[128];
     std::string rep;
-    for (int nmu : {1, 2, 4, 0})
+    for (int nmu : {1, 2, 4, 0, 8})
         for (int block : {64, 128, 256}) {
+            if (nmu == 8 && (sizeof(T) == 8 || block != 256)) continue;   // the link-centric kernel: float32, 256
             const StencilShape shp{nmu, block};
             auto run = [&]() {
-                if (nmu == 4) launch_lap_shape<T, LF, 4>(ctx, shp, X, Y, 1, 0.5, -0.0625, nullptr, 0.0, -1, st);
+                if (nmu == 8) launch_lap_lc(ctx, LF, (const float*)X, (float*)Y, 0.5, -0.0625, st);
+                else if (nmu == 4) launch_lap_shape<T, LF, 4>(ctx, shp, X, Y, 1, 0.5, -0.0625, nullptr, 0.0, -1, st);
                 else if (nmu == 2) launch_lap_shape<T, LF, 2>(ctx, shp, X, Y, 1, 0.5, -0.0625, nullptr, 0.0, -1, st);
                 else if (nmu == 0) launch_lap_shape<T, LF, 0>(ctx, shp, X, Y, 1, 0.5, -0.0625, nullptr, 0.0, -1, st);
                 else launch_lap_shape<T, LF, 1>(ctx, shp, X, Y, 1, 0.5, -0.0625, nullptr, 0.0, -1, st);

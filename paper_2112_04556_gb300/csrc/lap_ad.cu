@@ -10,21 +10,21 @@
 //   phase 1: thread (hop, site) loads one link -- U_h(x) for the forward hops h < 4, U_{h-4}(x - h) for the
 //            backward ones -- and stores Ad (forward) or Ad^T (backward) in shared memory, with the
 //            neighbour site of that hop;
-//   phase 2: thread (site, mu, half) accumulates rows 4 half .. 4 half + 3 of H(X_f)_mu for CH fields
-//            at a time over the 8 hops, reading the adjoint rows from shared memory (bank-conflict-free
-//            padding) and the neighbour values from global memory, then writes its quarter-row of Y_f and
-//            adds the per-field dots <Y,Y>, <Y,X> to per-warp float64 sums (deterministic order).
+//   phase 2: thread (site, mu, field parity) accumulates the 8 rows of H(X_f)_mu for the fields f of its
+//            parity, CH at a time over the 8 hops, reading the adjoint rows from shared memory (padded so
+//            that a warp's 128-bit reads hit distinct bank quads) and the neighbour values from global
+//            memory (each thread its own fields: no load is issued twice), then writes Y_f(x)_mu and adds the
+//            per-field dots <Y,Y>, <Y,X> to per-warp float64 sums (deterministic order).
 #include "common.cuh"
 #include "ops.cuh"
 
 namespace rm {
 
 constexpr int kAdSites = 32;                 // sites per tile
-constexpr int kAdThreads = 256;              // 8 hops x 32 sites in phase 1; 32 sites x 4 mu x 2 halves in phase 2
-constexpr int kAdHalf = 36;                  // floats per half record (4 rows x 8, padded by 4)
-constexpr int kAdHop = 2 * kAdHalf;          // floats per (site, hop) record
-constexpr int kAdSiteStride = 8 * kAdHop + 8;   // 584 floats: = 8 mod 32, so the 8 (site, half) records a warp
-                                                // reads in one 128-bit load fall on 8 distinct bank quads
+constexpr int kAdThreads = 256;              // 8 hops x 32 sites in phase 1; 32 sites x 4 mu x 2 parities in phase 2
+constexpr int kAdHop = 64;                   // floats per (site, hop) record: 8 rows x 8
+constexpr int kAdSiteStride = 8 * kAdHop + 8;   // 520 floats: = 8 mod 32, so the 4 site records a warp reads in one
+                                                // 128-bit load fall on distinct bank quads
 constexpr size_t kAdSmemFloats = (size_t)kAdSites * kAdSiteStride;
 constexpr int kMaxDevices = 64;
 
@@ -48,8 +48,8 @@ __global__ void __launch_bounds__(kAdThreads, MINB) k_lap_ad(Geom g, Links32 U, 
     if (DOTS)
         for (int i = t; i < (kAdThreads / 32) * nf * 2; i += kAdThreads) dsum[i] = 0.0;
     const int ntile = (g.V + kAdSites - 1) / kAdSites;
-    // phase-2 role of this thread
-    const int ps = t >> 3, pmu = (t >> 1) & 3, phalf = t & 1;
+    // phase-2 role of this thread: site, component, and the parity of its fields
+    const int ps = t >> 3, pmu = (t >> 1) & 3, par = t & 1;
     for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         // ---- phase 1: adjoint matrices of the 8 hops of every site in the tile
         {
@@ -64,12 +64,12 @@ __global__ void __launch_bounds__(kAdThreads, MINB) k_lap_ad(Geom g, Links32 U, 
                     // Ad row by row: column b lands in entry b of each row
                     adjoint_columns(u, [&](int bcol, const float (&col)[8]) {
 #pragma unroll
-                        for (int r = 0; r < 8; r++) rec[(r >> 2) * kAdHalf + (r & 3) * 8 + bcol] = col[r];
+                        for (int r = 0; r < 8; r++) rec[r * 8 + bcol] = col[r];
                     });
                 } else {
                     // Ad^T: column b of Ad is row b of the record
                     adjoint_columns(u, [&](int bcol, const float (&col)[8]) {
-                        float4* d = reinterpret_cast<float4*>(rec + (bcol >> 2) * kAdHalf + (bcol & 3) * 8);
+                        float4* d = reinterpret_cast<float4*>(rec + bcol * 8);
                         d[0] = make_float4(col[0], col[1], col[2], col[3]);
                         d[1] = make_float4(col[4], col[5], col[6], col[7]);
                     });
@@ -81,16 +81,18 @@ __global__ void __launch_bounds__(kAdThreads, MINB) k_lap_ad(Geom g, Links32 U, 
         // ---- phase 2
         const int s = tile * kAdSites + ps;
         const bool active = s < g.V;
-        const float* rec0 = ad + ps * kAdSiteStride + phalf * kAdHalf;
+        const float* rec0 = ad + ps * kAdSiteStride;
         const int* nb = nbr + ps * 8;
         const float* Xm = X + pmu * 8;
+        // fields of this thread: par, par + 2, par + 4, ...; pass p covers the CH fields par + 2 (p CH + q)
+        const int mine = (nf - par + 1) / 2;
         // the (pass, hop) iterations are software-pipelined: the neighbour values of the next iteration are
         // loaded before the arithmetic of the current one
-        auto load_x = [&](int f0, int hop, float (&x)[CH][8]) {
+        auto load_x = [&](int q0, int hop, float (&x)[CH][8]) {
             const size_t n = (size_t)nb[hop] * 32;
 #pragma unroll
             for (int q = 0; q < CH; q++) {
-                if (active && f0 + q < nf) load8(Xm + (size_t)(f0 + q) * fs + n, x[q]);
+                if (active && q0 + q < mine) load8(Xm + (size_t)(par + 2 * (q0 + q)) * fs + n, x[q]);
                 else
 #pragma unroll
                     for (int k = 0; k < 8; k++) x[q][k] = 0.f;
@@ -98,62 +100,71 @@ __global__ void __launch_bounds__(kAdThreads, MINB) k_lap_ad(Geom g, Links32 U, 
         };
         float xb[2][CH][8];
         load_x(0, 0, xb[0]);
-        for (int f0 = 0; f0 < nf; f0 += CH) {
-            float acc[CH][4];
+        const int npass = (mine + CH - 1) / CH;
+        const int npass_blk = ((nf + 1) / 2 + CH - 1) / CH;   // uniform over the block (for the dot shuffles)
+        for (int p = 0; p < npass_blk; p++) {
+            const int q0 = p * CH;
+            float acc[CH][8];
 #pragma unroll
             for (int q = 0; q < CH; q++)
 #pragma unroll
-                for (int r = 0; r < 4; r++) acc[q][r] = 0.f;
+                for (int r = 0; r < 8; r++) acc[q][r] = 0.f;
+            if (p < npass) {
 #pragma unroll
-            for (int hop = 0; hop < 8; hop++) {
-                // prefetch: the next hop of this pass, or hop 0 of the next pass
-                if (hop < 7) load_x(f0, hop + 1, xb[(hop + 1) & 1]);
-                else if (f0 + CH < nf) load_x(f0 + CH, 0, xb[0]);
-                const float (&x)[CH][8] = xb[hop & 1];
-                const float* rec = rec0 + hop * kAdHop;
+                for (int hop = 0; hop < 8; hop++) {
+                    // prefetch: the next hop of this pass, or hop 0 of the next pass
+                    if (hop < 7) load_x(q0, hop + 1, xb[(hop + 1) & 1]);
+                    else if (q0 + CH < mine) load_x(q0 + CH, 0, xb[0]);
+                    const float (&x)[CH][8] = xb[hop & 1];
+                    const float* rec = rec0 + hop * kAdHop;
 #pragma unroll
-                for (int r = 0; r < 4; r++) {
-                    const float4 r0 = *reinterpret_cast<const float4*>(rec + r * 8);
-                    const float4 r1 = *reinterpret_cast<const float4*>(rec + r * 8 + 4);
+                    for (int r = 0; r < 8; r++) {
+                        const float4 r0 = *reinterpret_cast<const float4*>(rec + r * 8);
+                        const float4 r1 = *reinterpret_cast<const float4*>(rec + r * 8 + 4);
 #pragma unroll
-                    for (int q = 0; q < CH; q++) {
-                        float v = acc[q][r];
-                        v = fmaf(r0.x, x[q][0], v); v = fmaf(r0.y, x[q][1], v);
-                        v = fmaf(r0.z, x[q][2], v); v = fmaf(r0.w, x[q][3], v);
-                        v = fmaf(r1.x, x[q][4], v); v = fmaf(r1.y, x[q][5], v);
-                        v = fmaf(r1.z, x[q][6], v); v = fmaf(r1.w, x[q][7], v);
-                        acc[q][r] = v;
+                        for (int q = 0; q < CH; q++) {
+                            float v = acc[q][r];
+                            v = fmaf(r0.x, x[q][0], v); v = fmaf(r0.y, x[q][1], v);
+                            v = fmaf(r0.z, x[q][2], v); v = fmaf(r0.w, x[q][3], v);
+                            v = fmaf(r1.x, x[q][4], v); v = fmaf(r1.y, x[q][5], v);
+                            v = fmaf(r1.z, x[q][6], v); v = fmaf(r1.w, x[q][7], v);
+                            acc[q][r] = v;
+                        }
                     }
                 }
             }
-            // epilogue: the thread's 4 components of Y_f(s)_mu, and the dots
+            // epilogue: Y_f(s)_mu for the pass's fields, and the dots (every lane joins the shuffles)
 #pragma unroll
             for (int q = 0; q < CH; q++) {
-                const int f = f0 + q;
+                const int fi = q0 + q;                 // index among this thread's fields
+                const int f = par + 2 * fi;
                 float yy = 0.f, yx = 0.f;
-                if (active && f < nf) {
-                    const size_t off = (size_t)f * fs + (size_t)s * 32 + pmu * 8 + phalf * 4;
-                    const float4 xo = __ldg(reinterpret_cast<const float4*>(X + off));
-                    float y[4] = {fmaf(b, acc[q][0], a * xo.x), fmaf(b, acc[q][1], a * xo.y),
-                                  fmaf(b, acc[q][2], a * xo.z), fmaf(b, acc[q][3], a * xo.w)};
+                if (active && fi < mine) {
+                    const size_t off = (size_t)f * fs + (size_t)s * 32 + pmu * 8;
+                    float xo[8], y[8];
+                    load8(X + off, xo);
+#pragma unroll
+                    for (int r = 0; r < 8; r++) y[r] = fmaf(b, acc[q][r], a * xo[r]);
                     if (HAS_W) {
-                        const float4 w = __ldg(reinterpret_cast<const float4*>(W + off));
-                        y[0] = fmaf(c, w.x, y[0]); y[1] = fmaf(c, w.y, y[1]);
-                        y[2] = fmaf(c, w.z, y[2]); y[3] = fmaf(c, w.w, y[3]);
+                        float w[8];
+                        load8(W + off, w);
+#pragma unroll
+                        for (int r = 0; r < 8; r++) y[r] = fmaf(c, w[r], y[r]);
                     }
-                    *reinterpret_cast<float4*>(Y + off) = make_float4(y[0], y[1], y[2], y[3]);
+                    store8(Y + off, y);
                     if (DOTS) {
-                        yy = fmaf(y[0], y[0], fmaf(y[1], y[1], fmaf(y[2], y[2], y[3] * y[3])));
-                        yx = fmaf(y[0], xo.x, fmaf(y[1], xo.y, fmaf(y[2], xo.z, y[3] * xo.w)));
+#pragma unroll
+                        for (int r = 0; r < 8; r++) { yy = fmaf(y[r], y[r], yy); yx = fmaf(y[r], xo[r], yx); }
                     }
                 }
-                if (DOTS && f < nf) {
+                if (DOTS) {
+                    // lanes of parity par hold field par + 2 fi: reduce each parity over its 16 lanes
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
+                    for (int o = 16; o > 1; o >>= 1) {
                         yy += __shfl_xor_sync(0xffffffffu, yy, o);
                         yx += __shfl_xor_sync(0xffffffffu, yx, o);
                     }
-                    if (lane == 0) {
+                    if (lane < 2 && par + 2 * fi < nf) {
                         dsum[(warp * nf + f) * 2] += (double)yy;
                         dsum[(warp * nf + f) * 2 + 1] += (double)yx;
                     }

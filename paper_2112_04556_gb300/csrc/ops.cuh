@@ -13,8 +13,13 @@ int launch_lap(rmhmc_ctx* ctx, int prec, int linkfmt, const void* X, void* Y, in
 // application, shared by all fields; dots as launch_lap
 int launch_lap_ad(rmhmc_ctx* ctx, int linkfmt, const float* X, float* Y, int nfield, double a, double b, const float* W,
                   double c, int slot, cudaStream_t st);
+// the link-centric adjoint stencil (lap_lc.cu), float32, one field: Y = a X + b H(X); and the CG stencil
+// q = diag r_k + (-1/16) H(r_k) + beta q (k from flags[1], as the gather kernel of krylov.cu)
+int launch_lap_lc(rmhmc_ctx* ctx, int linkfmt, const float* X, float* Y, double a, double b, cudaStream_t st);
+int launch_cg_lc(rmhmc_ctx* ctx, const float* R, float* q, double diag, const int* flags, double* vals, int maxit,
+                 double* partials, unsigned* counter, cudaStream_t st);
 // fewest fields for which launch_lap takes the adjoint form
-constexpr int kAdMinFields = 2;
+constexpr int kAdMinFields = 6;
 
 // gauge force F = -dS/dw (float64 output; arithmetic float64 or float32) from the context's links
 int gauge_force_launch(rmhmc_ctx* ctx, double beta, double c1, int prec, double* F, cudaStream_t st);

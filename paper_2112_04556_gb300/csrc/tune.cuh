@@ -9,7 +9,7 @@
 namespace rm {
 
 // nmu: components per lane (1, 2, 4), or 0 for one component per lane with all neighbour values
-// prefetched before the arithmetic
+// prefetched before the arithmetic, or 8 for the link-centric adjoint kernel (float32, 4D boxes swept in t)
 struct StencilShape {
     int nmu = 1;
     int block = 128;
@@ -21,7 +21,7 @@ template <typename T, int NMU> constexpr int stencil_min_blocks() {
     return sizeof(T) == 8 ? 1 : NMU == 1 ? 4 : NMU == 4 ? 2 : 3;
 }
 
-inline int lanes_per_site(int nmu) { return nmu == 0 ? 4 : 4 / nmu; }
+inline int lanes_per_site(int nmu) { return nmu == 0 ? 4 : nmu == 8 ? 4 : 4 / nmu; }
 
 // shape for (sizeof(T), LF); tunes on first use
 template <typename T, int LF>

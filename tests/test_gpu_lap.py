@@ -21,12 +21,12 @@ def _run(ctx, U_d, X, prec, linkfmt, op=0):
 
 @pytest.mark.parametrize("L", [(4, 4, 4, 4), (2, 4, 6, 8), (5, 3, 4, 7), (3, 3, 3, 3)])
 def test_lap_parity_small(L):
-    """Several 128-site tiles and a ragged last tile (5x3x4x7 = 420 sites); odd extents included.  Five
-    fields: the float32 paths take the multi-field adjoint form (tiles of 32 sites, fields in passes of 3,
-    so the last pass is ragged too)."""
+    """Several 128-site tiles and a ragged last tile (5x3x4x7 = 420 sites); odd extents included.  Seven
+    fields: the float32 paths take the multi-field adjoint form (tiles of 32 sites, fields split by parity and
+    taken in passes, so the last pass is ragged too)."""
     import paper_2112_04556_gb300 as rm
     U = inputs.random_links(L, eps=0.7, seed=1)
-    X = inputs.gaussian_fields(L, 5, seed=2)
+    X = inputs.gaussian_fields(L, 7, seed=2)
     ref = oracle.lap(L, U, X)
     with rm.Context(L) as ctx:
         Ud = dev(U)
@@ -102,7 +102,7 @@ def test_lap_errors_and_empty():
         assert code == rm.OK                          # nothing to do for zero fields
 
 
-@pytest.mark.parametrize("nf", [2, 4])
+@pytest.mark.parametrize("nf", [2, 6, 9])
 def test_lap_multifield_full_size_sampled(nf):
     """32^4, several float32 fields in one launch (the adjoint form), 18- and 12-real links, on sampled sites
     of every field; each field also equals its own single-field application to float32 rounding."""
@@ -124,3 +124,57 @@ def test_lap_multifield_full_size_sampled(nf):
                 assert rel_l2(Y[f][sites], refs[f]) <= 1e-5, (lf, f)
             Y1 = host(rm.lap_apply(ctx, None, X32[nf - 1].contiguous(), prec=rm.FP32, linkfmt=lf)).astype(np.float64)
             assert rel_l2(Y[nf - 1], Y1) <= 2e-6
+
+
+# every pinned float32 shape, including the link-centric adjoint kernel (nmu 8): boxes of 8 x 4 x 2 sites
+# swept through t-ranges of 8 slices, so these extents give full boxes (wrap inside the box), partial last
+# boxes (10 = 8 + 2, 9 = 8 + 1 slices), extents 2 (both neighbours the same site) and 3
+SHAPES = [(8, 256), (2, 256), (0, 128), (1, 64), (4, 256)]
+
+
+@pytest.mark.parametrize("L", [(4, 4, 4, 4), (5, 3, 4, 7), (2, 4, 6, 8), (3, 3, 3, 3), (10, 6, 5, 9), (8, 4, 2, 17)])
+def test_lap_every_shape(L):
+    import paper_2112_04556_gb300 as rm
+    torch = torch_cuda()
+    U = inputs.random_links(L, eps=0.7, seed=11)
+    X = inputs.gaussian_fields(L, 1, seed=12)[0]
+    ref = oracle.lap(L, U, X)
+    X32 = dev(X, torch.float32)
+    for nmu, block in SHAPES:
+        with rm.Context(L) as ctx:
+            for lf in (18, 12):
+                rm.set_stencil_shape(ctx, rm.SHAPE_LAP, rm.FP32, lf, nmu, block)
+            Ud = dev(U)
+            for lf in (18, 12):
+                Y = host(rm.lap_apply(ctx, Ud, X32, prec=rm.FP32, linkfmt=lf)).astype(np.float64)
+                assert rel_l2(Y, ref) <= 1e-5, (nmu, lf, rel_l2(Y, ref))
+            # Delta itself through the same shape
+            Y = host(rm.lap_apply(ctx, None, X32, prec=rm.FP32, op=rm.OP_DELTA)).astype(np.float64)
+            assert rel_l2(Y, -16.0 * ref) <= 1e-5
+
+
+def test_lap_link_centric_full_size_sampled():
+    """The link-centric kernel at 32^4 and 24^3 x 48 on sampled sites (every box full, t-ranges of 8)."""
+    import paper_2112_04556_gb300 as rm
+    torch = torch_cuda()
+    for L in [(32, 32, 32, 32), (24, 24, 24, 48)]:
+        U = inputs.random_links(L, eps=0.3, seed=0)
+        X = inputs.gaussian_fields(L, 1, seed=4)[0]
+        rng = np.random.default_rng(5)
+        V = int(np.prod(L))
+        sites = np.unique(np.concatenate([rng.integers(0, V, 3000), [0, V - 1], np.arange(V - 64, V)]))
+        ref = oracle.lap_sites(L, U, X, sites)
+        with rm.Context(L) as ctx:
+            for lf in (18, 12):
+                rm.set_stencil_shape(ctx, rm.SHAPE_LAP, rm.FP32, lf, 8, 256)
+                Y = host(rm.lap_apply(ctx, dev(U), dev(X, torch.float32), prec=rm.FP32, linkfmt=lf)).astype(np.float64)
+                assert rel_l2(Y[sites], ref) <= 1e-5, (L, lf)
+
+
+def test_set_stencil_shape_rejects():
+    import paper_2112_04556_gb300 as rm
+    with rm.Context((4, 4, 4, 4)) as ctx:
+        for args in [(2, rm.FP32, 18, 1, 128), (0, rm.FP64, 18, 8, 256), (0, rm.FP32, 18, 8, 128),
+                     (1, rm.FP32, 12, 2, 256), (0, rm.FP32, 18, 3, 256), (0, rm.FP32, 18, 2, 100)]:
+            with pytest.raises(rm.RmhmcError):
+                rm.set_stencil_shape(ctx, *args)

@@ -179,3 +179,64 @@ def test_spectrum_fitted_mass_trajectory():
     r = out[rm.FP64]
     assert abs(r["T0"] - 0.5 * float((xi * xi).sum())) <= 1e-9 * r["T0"]
     assert np.isfinite(r["dH"]) and abs(out[rm.MIXED]["dH"] - r["dH"]) <= 1e-2 * max(1.0, abs(r["dH"]))
+
+
+def test_basis_cap_restarts_fitted_mass_16_4():
+    """A spectrum-fitted mass with poles down to sigma = 1e-3 on smooth 16^4 links (random SU(3) close to 1,
+    so A keeps eigenvalues near 0 and A + 1e-3 has a condition number near 10^3; on the thermalised links the
+    adjoint Laplacian has a gap and the solves stay short), where the smallest shift needs more Krylov
+    iterations than the 160 stored residuals: the first pass stops at the cap and the reliable-update loop
+    continues from the true residuals (restarts).  Every shifted solution is checked against the oracle's own
+    operator, |b - (A + sigma_j) x_j| / |b| with A applied by the oracle; a float64 single shift at 1e-3 to
+    1e-12 must need more than 160 iterations.  The kinetic force of the MD, which has no restarts, either
+    converges within the cap or reports ENOCONV."""
+    import paper_2112_04556_gb300 as rm
+    L = (16, 16, 16, 16)
+    U = inputs.random_links(L, eps=0.05, seed=90)
+    lam = (np.arange(64) + 0.5) / 64
+    m = rm.mass_fit_spectrum(lam, lam, 12, 1e-3, 10.0)
+    assert min(m["sigma"]) <= 1.1e-3
+    b = inputs.gaussian_fields(L, 1, seed=91)[0]
+    nb = np.linalg.norm(b)
+    with rm.Context(L) as ctx:
+        Ud = dev(U)
+        y, xs, iters, resid = rm.rat_mass_solve(ctx, Ud, dev(b), m, tol=1e-10, prec=rm.MIXED, want_xs=True)
+        assert np.all(resid <= 1e-10), resid
+        xs = host(xs)
+        for j in range(len(m["sigma"])):
+            r = b - (oracle.lap(L, U, xs[j]) + m["sigma"][j] * xs[j])
+            assert np.linalg.norm(r) / nb <= 2e-10, (j, np.linalg.norm(r) / nb)
+        y_ref = m["c"] * b + sum(m["alpha"][j] * xs[j] for j in range(len(m["sigma"])))
+        assert rel_l2(host(y), y_ref) <= 1e-12
+        single = {"c": 0.0, "alpha": [1.0], "sigma": [1e-3]}
+        y1, _, it1, res1 = rm.rat_mass_solve(ctx, None, dev(b), single, tol=1e-12, prec=rm.FP64)
+        assert it1 > 160 and res1[0] <= 1e-12, (it1, res1)
+        r = b - (oracle.lap(L, U, host(y1)) + 1e-3 * host(y1))
+        assert np.linalg.norm(r) / nb <= 2e-12
+        try:
+            F, _, _ = rm.kinetic_force(ctx, None, dev(b), m, tol=1e-6, prec=rm.MIXED)
+            assert np.all(np.isfinite(host(F)))
+        except rm.RmhmcError as e:
+            assert e.code == rm.ENOCONV and "cap" in str(e)
+
+
+@pytest.mark.parametrize("nmu,block", [(8, 256), (2, 256), (0, 64)])
+def test_cg_stencil_shapes(nmu, block):
+    """The mixed solve through each pinned CG stencil shape, the link-centric kernel included, on a lattice
+    with partial boxes and t-ranges (10 x 6 x 5 x 9): parity with the oracle's per-shift solves at 1e-10."""
+    import paper_2112_04556_gb300 as rm
+    L = (10, 6, 5, 9)
+    U = inputs.random_links(L, eps=0.5, seed=27)
+    b = inputs.gaussian_fields(L, 1, seed=28)[0]
+    m = fit.mass_term(12, 0.9)
+    y_ref, _ = oracle.rational_apply(L, U, b, m, tol=1e-14)
+    with rm.Context(L) as ctx:
+        rm.set_stencil_shape(ctx, rm.SHAPE_CG, rm.FP32, 18, nmu, block)
+        y, _, iters, resid = rm.rat_mass_solve(ctx, dev(U), dev(b), m, tol=1e-10, prec=rm.MIXED)
+        assert np.all(resid <= 1e-10) and iters > 0
+        assert rel_l2(host(y), y_ref) <= 1e-9
+        F, Vel, T = rm.kinetic_force(ctx, None, dev(b), m, tol=1e-7, prec=rm.MIXED)
+        rm.set_stencil_shape(ctx, rm.SHAPE_CG, rm.FP32, 18, 2, 256)
+        F2, Vel2, T2 = rm.kinetic_force(ctx, None, dev(b), m, tol=1e-7, prec=rm.MIXED)
+    assert rel_l2(host(F), host(F2)) <= 1e-5 and rel_l2(host(Vel), host(Vel2)) <= 1e-5
+    assert abs(T - T2) <= 1e-6 * abs(T2)
