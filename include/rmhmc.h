@@ -186,13 +186,17 @@ int rmhmc_set_graphs(rmhmc_ctx* ctx, int on);
 int rmhmc_tuning(const rmhmc_ctx* ctx, char* buf, int len);
 
 /* Pin a stencil launch shape instead of timing the candidates: kernel = RMHMC_SHAPE_LAP (lap_apply and the
- * float32 recurrence of one field) or RMHMC_SHAPE_CG (the conjugate-gradient stencil), for precision prec
+ * float32 recurrence of one field), RMHMC_SHAPE_CG (the conjugate-gradient stencil) or RMHMC_SHAPE_KFORCE (see
+ * below), for precision prec
  * (RMHMC_FP64 / RMHMC_FP32) and link format linkfmt (the CG stencil streams 18-real links: 18 only).
  * nmu: components per lane (1, 2, 4), 0 (one component per lane with every neighbour value prefetched) or
  * 8 (the link-centric adjoint kernel: each link's adjoint matrix serves both hops across it, in 4D boxes
  * swept through time; float32 only, block 256); block: 64, 128 or 256 threads.  RMHMC_EINVAL otherwise. */
 #define RMHMC_SHAPE_LAP 0
 #define RMHMC_SHAPE_CG  1
+#define RMHMC_SHAPE_KFORCE 2   /* the mixed kinetic force's basis contraction: nmu 1 stages the block's own basis
+                                  rows in shared memory (runs of up to 20 vectors), nmu 0 (the default) reads
+                                  them from global memory once per chunk; prec RMHMC_FP32, linkfmt 18, block 128 */
 int rmhmc_set_stencil_shape(rmhmc_ctx* ctx, int kernel, int prec, int linkfmt, int nmu, int block);
 
 /* ---------------------------------------------------------------------------------------------- */

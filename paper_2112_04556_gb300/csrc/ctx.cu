@@ -228,6 +228,12 @@ extern "C" int rmhmc_tuning(const rmhmc_ctx* ctx, char* buf, int len) {
 extern "C" int rmhmc_set_stencil_shape(rmhmc_ctx* ctx, int kernel, int prec, int linkfmt, int nmu, int block) {
     if (!ctx) return RMHMC_EINVAL;
     ctx->err.clear();
+    if (kernel == RMHMC_SHAPE_KFORCE) {
+        if (prec != RMHMC_FP32 || linkfmt != 18 || (nmu != 0 && nmu != 1) || block != 128)
+            return set_err(ctx, RMHMC_EINVAL, "kinetic-force contraction: RMHMC_FP32, 18, nmu 0 or 1, block 128");
+        ctx->lg_staged = nmu == 1;
+        return RMHMC_OK;
+    }
     if (kernel != RMHMC_SHAPE_LAP && kernel != RMHMC_SHAPE_CG) return set_err(ctx, RMHMC_EINVAL, "bad kernel");
     if (prec != RMHMC_FP64 && prec != RMHMC_FP32) return set_err(ctx, RMHMC_EINVAL, "bad prec");
     if (linkfmt != 18 && (linkfmt != 12 || kernel == RMHMC_SHAPE_CG)) return set_err(ctx, RMHMC_EINVAL, "bad linkfmt");

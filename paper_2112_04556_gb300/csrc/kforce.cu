@@ -250,6 +250,126 @@ __global__ void __launch_bounds__(kLgSites * 4, 4) k_link_grad_krylov(Geom g, ty
     }
 }
 
+// The same contraction with the block's own basis rows staged once in shared memory (for n <= kLgStage):
+// the kernel above reads r_l(y) for all l once per chunk of kLgKC basis vectors, i.e. n / kLgKC times from
+// L2; here the 32 sites' n rows are copied in once (coalesced 16-byte loads, site records padded to 36
+// floats so that a warp's 128-bit reads fall on distinct bank quads) and every chunk reads them from shared
+// memory.  In the C phase the next neighbour row is loaded before the arithmetic of the current one.
+// Longer runs (n > kLgStage, read on the device) take the global reads of the kernel above.
+constexpr int kLgStage = 20;
+constexpr int kLgRow = 36;   // floats per staged site row (32 + 4)
+
+inline size_t lg_staged_smem() {
+    return sizeof(float) * ((size_t)kLgStage * kLgSites * kLgRow + kLgSites * kLgPad + kLgKC * kBasisCap);
+}
+
+template <int LF>
+__global__ void __launch_bounds__(kLgSites * 4, 2) k_link_grad_staged(Geom g, Links32 U, const float* __restrict__ R,
+                                                                      size_t fs, const int* __restrict__ flags, int n,
+                                                                      const double* __restrict__ S, int ld,
+                                                                      double* __restrict__ G) {
+    extern __shared__ __align__(16) float lgs[];
+    float* Rs = lgs;                                          // [kLgStage][kLgSites][kLgRow]
+    float* Ws = Rs + (size_t)kLgStage * kLgSites * kLgRow;    // [kLgSites][kLgPad]
+    float* Ss = Ws + kLgSites * kLgPad;                       // [kLgKC][kBasisCap]
+    if (flags) n = flags[1];
+    const bool staged = n <= kLgStage;
+    const int sl = threadIdx.x >> 2, q = threadIdx.x & 3;
+    float* const wrow = Ws + sl * kLgPad;
+    for (int base = blockIdx.x * kLgSites; base < g.V; base += gridDim.x * kLgSites) {
+        const int y = base + sl;
+        const bool live = y < g.V;
+        const int yn = live ? step_site(g, y, q, 1) : 0;
+        if (staged) {
+            __syncthreads();   // the previous tile's reads of Rs are done
+            const int nsite = min(kLgSites, g.V - base);
+            for (int idx = threadIdx.x; idx < n * kLgSites * 8; idx += blockDim.x) {
+                const int l = idx / (kLgSites * 8), rem = idx - l * (kLgSites * 8);
+                const int ss = rem >> 3, c4 = rem & 7;
+                if (ss < nsite) {
+                    const float4 v = __ldg(reinterpret_cast<const float4*>(R + (size_t)l * fs + (size_t)(base + ss) * 32) + c4);
+                    *reinterpret_cast<float4*>(Rs + ((size_t)l * kLgSites + ss) * kLgRow + c4 * 4) = v;
+                }
+            }
+        }
+        float C[8][8];
+#pragma unroll
+        for (int b = 0; b < 8; b++)
+#pragma unroll
+            for (int d = 0; d < 8; d++) C[b][d] = 0.f;
+        for (int k0 = 0; k0 < n; k0 += kLgKC) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < kLgKC * n; t += blockDim.x) {
+                const int kk = t / n, l = t - kk * n;
+                Ss[kk * kBasisCap + l] = k0 + kk < n ? (float)S[(size_t)(k0 + kk) * ld + l] : 0.f;
+            }
+            __syncthreads();
+            float w[kLgKC][8];
+#pragma unroll
+            for (int kk = 0; kk < kLgKC; kk++)
+#pragma unroll
+                for (int a = 0; a < 8; a++) w[kk][a] = 0.f;
+            if (live) {
+                for (int l = 0; l < n; l++) {
+                    float r[8];
+                    if (staged) lds8(Rs + ((size_t)l * kLgSites + sl) * kLgRow + q * 8, r);
+                    else load8_v8(R + (size_t)l * fs + (size_t)y * 32 + q * 8, r);
+#pragma unroll
+                    for (int kk = 0; kk < kLgKC; kk++) {
+                        const float sv = Ss[kk * kBasisCap + l];
+#pragma unroll
+                        for (int a = 0; a < 8; a++) w[kk][a] = fmaf(sv, r[a], w[kk][a]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < kLgKC; kk++) store8(wrow + kk * 32 + q * 8, w[kk]);
+            __syncthreads();
+            if (live) {
+                const int kc = min(kLgKC, n - k0);
+                // neighbour rows of the chunk, one (k, mu) ahead: iterations it = 4 kk + mu in pairs, the even
+                // one in ra, the odd one in rb
+                const float* rn = R + (size_t)k0 * fs + (size_t)yn * 32;   // (k0 + kk, mu) at rn + kk fs + 8 mu
+                auto contract = [&](const float (&rv)[8], int it) {
+                    float wv[8];
+                    lds8(wrow + (it >> 2) * 32 + (it & 3) * 8, wv);
+#pragma unroll
+                    for (int b = 0; b < 8; b++)
+#pragma unroll
+                        for (int d = 0; d < 8; d++) C[b][d] = fmaf(rv[b], wv[d], C[b][d]);
+                };
+                float ra[8], rb[8];
+                load8_v8(rn, ra);
+                for (int it = 0; it < 4 * kc; it += 2) {
+                    load8_v8(rn + (size_t)((it + 1) >> 2) * fs + ((it + 1) & 3) * 8, rb);   // it + 1 < 4 kc always
+                    contract(ra, it);
+                    if (it + 2 < 4 * kc) load8_v8(rn + (size_t)((it + 2) >> 2) * fs + ((it + 2) & 3) * 8, ra);
+                    contract(rb, it + 1);
+                }
+            }
+        }
+        if (live) {
+            const mat3<float> u = LinkLoad<float, LF>::load(U, y, q);
+            float Gk[8];
+#pragma unroll
+            for (int a = 0; a < 8; a++) Gk[a] = 0.f;
+#pragma unroll
+            for (int d = 0; d < 8; d++) {
+                float col[8], rc[8];
+#pragma unroll
+                for (int b = 0; b < 8; b++) col[b] = C[b][d];
+                herm<float> E = h_zero<float>();
+                acc_uxud(E, u, coef_to_herm2(col));   // 2 sum_c (R C)_cd T^c
+                herm2_to_coef(E, rc);                  // (R C)_cd
+                f_contract(d, rc, Gk);
+            }
+            double* out = G + (size_t)y * 32 + q * 8;
+#pragma unroll
+            for (int a = 0; a < 8; a++) out[a] = (double)Gk[a] * (1.0 / 16.0);
+        }
+    }
+}
+
 // F_K from the basis rows (X_j rows 0..ns-1, Z_j rows ns..2ns-1, row stride ldr, device float64) of the
 // float32 basis R; n on the host, or read on the device from flags[1] when flags is given
 int link_grad_krylov_launch(rmhmc_ctx* ctx, const float* R, const double* rows, int ldr, int ns, const double* alpha,
@@ -262,9 +382,26 @@ int link_grad_krylov_launch(rmhmc_ctx* ctx, const float* R, const double* rows, 
     for (int j = 0; j < ns; j++) pw.w[j] = alpha[j];
     k_pair_matrix<<<ctx->num_sms / 4 > 1 ? ctx->num_sms / 4 : 1, 256, 0, st>>>(rows, ldr, ns, pw, flags, n, S, kBasisCap);
     ++ctx->launches;
-    const int grid = capped_grid(ctx, (size_t)ctx->g.V * 4, kLgSites * 4);
-    k_link_grad_krylov<float, 18><<<grid, kLgSites * 4, 0, st>>>(ctx->g, links32(ctx), R, field_elems(ctx), flags, n, S,
-                                                                 kBasisCap, F);
+    if (ctx->lg_staged) {
+        static bool configured[64] = {};
+        if (ctx->device < 0 || ctx->device >= 64) return set_err(ctx, RMHMC_EINVAL, "device index too large");
+        if (!configured[ctx->device]) {
+            RM_CHECK(ctx, cudaFuncSetAttribute(k_link_grad_staged<18>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)lg_staged_smem()));
+            configured[ctx->device] = true;
+        }
+        int per_sm = 0;
+        RM_CHECK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_link_grad_staged<18>, kLgSites * 4,
+                                                                    lg_staged_smem()));
+        const int ntile = (ctx->g.V + kLgSites - 1) / kLgSites;
+        const int grid = std::max(1, std::min(ntile, (int)ctx->num_sms * std::max(per_sm, 1)));
+        k_link_grad_staged<18><<<grid, kLgSites * 4, lg_staged_smem(), st>>>(ctx->g, links32(ctx), R, field_elems(ctx),
+                                                                             flags, n, S, kBasisCap, F);
+    } else {
+        const int grid = capped_grid(ctx, (size_t)ctx->g.V * 4, kLgSites * 4);
+        k_link_grad_krylov<float, 18><<<grid, kLgSites * 4, 0, st>>>(ctx->g, links32(ctx), R, field_elems(ctx), flags, n,
+                                                                     S, kBasisCap, F);
+    }
     ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     return RMHMC_OK;

@@ -7,16 +7,18 @@
 //
 // The backward contributions travel to the neighbouring site, so the lattice is cut into 4D-blocked tiles
 // that sweep through time: a block owns an xyz box of sites (up to 8 x 4 x 2) and walks its t-range one
-// slice at a time.  Four threads per site, one per link direction nu.  Per slice:
-//   * the own field X(x) is staged in shared memory (transposed per colour component);
-//   * thread (x, nu) streams the rows of Ad(U_nu(x)) -- built as the columns of Ad(U^dag) -- and forms the
-//     forward rows (to shared memory, summed over nu later) and accumulates B in registers;
-//   * B goes to the slot of the target site in shared memory when the target lies in the box, and to a
-//     double-buffered slot for the next slice when nu = t;
-//   * the box's low faces take their backward contributions from links outside the box: extra threads
-//     recompute those (the halo), and the first slice of a t-range recomputes its t-halo;
-//   * thread (x, mu) then sums its component and applies the epilogue (lap_apply: Y = a X + b H; the CG
-//     stencil: q = (0.5 + sigma0) r - H(r)/16 + beta q_old with the dot <r, q>).
+// slice at a time, four threads per site (one per link direction nu).  Per slice:
+//   * the field of the box and of its one-site halo (the sites one step beyond each face) sits in shared
+//     memory, copied in asynchronously (cp.async) while the previous slice computes (double buffer);
+//   * the links of the slice were loaded into registers during the previous slice's epilogue, and so was
+//     X(x, t+1) for the t-direction thread;
+//   * halo first: the box's low faces get their backward contributions from links outside the box, each
+//     such link split over four threads by field component so that every thread has at most one task;
+//   * thread (x, nu) streams the rows of Ad(U_nu(x)) (the columns of Ad(U^dag)); each forward row is summed
+//     over the four link directions of the site with a fixed 3-shuffle transpose-sum, and B accumulates in
+//     registers and goes to the shared slot of the target site (the next slice's slot when nu = t);
+//   * thread (x, mu) applies the epilogue (lap_apply: Y = a X + b H; the CG stencil:
+//     q = (0.5 + sigma0) r - H(r)/16 + beta q_old with the dot <r, q>).
 // Every slot is written exactly once per slice, and every sum has a fixed order (deterministic results).
 #include "common.cuh"
 #include "ops.cuh"
@@ -28,14 +30,13 @@ constexpr int kLcSites = 64;                 // sites per box
 constexpr int kLcThreads = 4 * kLcSites;     // one thread per (site, link direction)
 constexpr int kLcBox[3] = {8, 4, 2};         // box extents in x, y, z (clipped to the lattice)
 constexpr int kLcTLen = 8;                   // slices per t-range
-// shared-memory layout (floats); the paddings keep the 128-bit reads and the scalar writes of a warp on
-// distinct bank quads
-constexpr int kLcXO = 36;                    // own field per site: [a][mu] (8 x 4) + 4
-constexpr int kLcFS = 164;                   // forward rows per site: [mu][a][nu] at mu stride 36, + pad (= 4 mod 32)
-constexpr int kLcFmu = 36;
+constexpr int kLcFaceMax = 8 + 16 + 32;      // face sites of the largest box (4x2 + 8x2 + 8x4)
+constexpr int kLcSlots = kLcSites + 2 * kLcFaceMax;   // field slots: box, high-face and low-face neighbours
+// shared-memory layout (floats); the paddings keep a warp's 128-bit reads on distinct bank quads
+constexpr int kLcRow = 36;                   // field slot: [mu][a] (32) + 4
 constexpr int kLcBS = 100;                   // backward slots per site: [d = x, y, z][mu][8] + 4
 constexpr int kLcBT = 36;                    // t-backward slot per site: [mu][8] + 4
-constexpr int kLcSmemFloats = kLcSites * (kLcXO + kLcFS + kLcBS + 2 * kLcBT);
+constexpr int kLcSmemFloats = 2 * kLcSlots * kLcRow + kLcSites * kLcBS + 2 * kLcSites * kLcBT + kLcSlots;
 
 struct LcGeom {
     int b[3];       // box extents
@@ -59,24 +60,41 @@ inline int lc_blocks(const Geom& g) {
     return lg.nb[0] * lg.nb[1] * lg.nb[2] * lg.nt;
 }
 
-// B = Ad(u)^T x for the four components (x[mu][a] in registers), rows of Ad streamed
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// rows of Ad(u), streamed (column a of Ad(u^dag) is row a of Ad(u))
 template <class RowSink>
 __device__ __forceinline__ void lc_rows(const mat3<float>& u, RowSink&& sink) {
-    adjoint_columns(m_dag(u), sink);   // column a of Ad(U^dag) is row a of Ad(U)
+    adjoint_columns(m_dag(u), sink);
 }
 
-// MODE 0: Y = a X + b H(X).  MODE 1: q = c0 r + b H(r) + beta q_old (k > 0), gamma = <r, q> (CG stencil;
+// sum over the four link-direction lanes of a site of f[mu], returned in the lane whose nu equals mu
+// (fixed order: pairs across bit 1 first, then across bit 0)
+__device__ __forceinline__ float quad_transpose_sum(const float (&f)[4], int nu) {
+    const bool hi = nu & 2, odd = nu & 1;
+    const float r0 = __shfl_xor_sync(0xffffffffu, hi ? f[0] : f[2], 2);
+    const float r1 = __shfl_xor_sync(0xffffffffu, hi ? f[1] : f[3], 2);
+    const float k0 = (hi ? f[2] : f[0]) + r0, k1 = (hi ? f[3] : f[1]) + r1;
+    const float r = __shfl_xor_sync(0xffffffffu, odd ? k0 : k1, 1);
+    return (odd ? k1 : k0) + r;
+}
+
+// MODE 0: Y = a X + b H(X).  MODE 1: q = a r + b H(r) + beta q_old (k > 0), gamma = <r, q> (CG stencil;
 // X = r_k is basis vector k of R, flags/vals as in k_cg_A)
 template <int LF, int MODE>
-__global__ void __launch_bounds__(kLcThreads, 2) k_lap_lc(Geom g, LcGeom lg, Links32 U, const float* __restrict__ Xin,
+__global__ void __launch_bounds__(kLcThreads, 1) k_lap_lc(Geom g, LcGeom lg, Links32 U, const float* __restrict__ Xin,
                                                           float* __restrict__ Y, float a, float b, size_t fs,
                                                           const int* __restrict__ flags, double* vals, int maxit,
                                                           double* partials, unsigned* counter) {
     extern __shared__ __align__(16) float sm[];
-    float* XO = sm;                                   // [site][kLcXO]
-    float* FS = XO + kLcSites * kLcXO;                // [site][kLcFS]
-    float* BS = FS + kLcSites * kLcFS;                // [site][kLcBS]
-    float* BT = BS + kLcSites * kLcBS;                // [2][site][kLcBT]
+    float* XO = sm;                                       // [2][kLcSlots][kLcRow]
+    float* BS = XO + 2 * kLcSlots * kLcRow;               // [site][kLcBS]
+    float* BT = BS + kLcSites * kLcBS;                    // [2][site][kLcBT]
+    int* slot_xyz = reinterpret_cast<int*>(BT + 2 * kLcSites * kLcBT);   // [kLcSlots]: xyz part of each slot's site
     __shared__ double sh[kLcThreads / 32];
     const float* X = Xin;
     float beta = 0.f;
@@ -101,170 +119,224 @@ __global__ void __launch_bounds__(kLcThreads, 2) k_lap_lc(Geom g, LcGeom lg, Lin
     const bool fx = lg.full[0], fy = lg.full[1], fz = lg.full[2];
     const int nsite = ex * ey * ez;
     const int t0 = tr * kLcTLen, t1 = min(g.L[3], t0 + kLcTLen);
-    const bool live = s < nsite;
-    int ix = 0, iy = 0, iz = 0;
-    if (live) { ix = s % ex; iy = (s / ex) % ey; iz = s / (ex * ey); }
-    const int gx = c0x + ix, gy = c0y + iy, gz = c0z + iz;
-    const int xyz = gx + g.L[0] * (gy + g.L[1] * gz);
     const int slice = g.stride[3];
-    // local index of the box site one step forward along d < 3 (-1 when it lies outside the box)
-    auto fwd_local = [&](int d) {
-        int jx = ix, jy = iy, jz = iz;
-        if (d == 0) { jx++; if (jx >= ex) { if (!fx) return -1; jx = 0; } }
-        else if (d == 1) { jy++; if (jy >= ey) { if (!fy) return -1; jy = 0; } }
-        else { jz++; if (jz >= ez) { if (!fz) return -1; jz = 0; } }
-        return jx + ex * (jy + ey * jz);
-    };
-    // the xyz part of the site one step forward along d < 3, periodic
-    auto fwd_xyz = [&](int d) {
-        if (d == 0) return gx + 1 == g.L[0] ? xyz - gx : xyz + 1;
-        if (d == 1) return gy + 1 == g.L[1] ? xyz - gy * g.stride[1] : xyz + g.stride[1];
-        return gz + 1 == g.L[2] ? xyz - gz * g.stride[2] : xyz + g.stride[2];
-    };
-    // halo tasks of a slice: the low faces of the box along x, y, z that are not full (one link each)
+    const int Lt = g.L[3];
+    // face sizes (0 along a direction the box spans) and their offsets in the slot list
     const int hx = fx ? 0 : ey * ez, hy = fy ? 0 : ex * ez, hz = fz ? 0 : ex * ey;
     const int nhalo = hx + hy + hz;
-    // B = Ad(U_d(site))^T X(site) into dst[mu * 8 + b]
-    auto backward_only = [&](int lsite, int d, float* dst) {
-        const mat3<float> u = LinkLoad<float, LF>::load(U, lsite, d);
-        float xo[4][8];
+    const int hiB = kLcSites, loB = kLcSites + nhalo;     // first high-face and low-face slot
+    // xyz index of the lattice site at box coordinates (jx, jy, jz) shifted by n along d (periodic)
+    auto site_xyz = [&](int jx, int jy, int jz, int d, int n) {
+        int gx = c0x + jx, gy = c0y + jy, gz = c0z + jz;
+        if (d == 0) { gx += n; gx = gx < 0 ? gx + g.L[0] : gx >= g.L[0] ? gx - g.L[0] : gx; }
+        else if (d == 1) { gy += n; gy = gy < 0 ? gy + g.L[1] : gy >= g.L[1] ? gy - g.L[1] : gy; }
+        else if (d == 2) { gz += n; gz = gz < 0 ? gz + g.L[2] : gz >= g.L[2] ? gz - g.L[2] : gz; }
+        return gx + g.L[0] * (gy + g.L[1] * gz);
+    };
+    // face index f (< hx, hy or hz) of direction d -> box coordinates of the face site (i_d = i)
+    auto face_site = [&](int d, int f, int i, int& jx, int& jy, int& jz) {
+        if (d == 0) { jx = i; jy = f % ey; jz = f / ey; }
+        else if (d == 1) { jy = i; jx = f % ex; jz = f / ex; }
+        else { jz = i; jx = f % ex; jy = f / ex; }
+    };
+    // slot table: box sites, then the sites one step beyond the high faces, then one step below the low faces
+    for (int sl = tid; sl < kLcSlots; sl += kLcThreads) {
+        int v = -1;
+        if (sl < nsite) {
+            v = site_xyz(sl % ex, (sl / ex) % ey, sl / (ex * ey), 3, 0);
+        } else if (sl >= hiB && sl < hiB + 2 * nhalo) {
+            const bool high = sl < loB;
+            int f = sl - (high ? hiB : loB), d = 0;
+            if (f >= hx) { f -= hx; d = 1; if (f >= hy) { f -= hy; d = 2; } }
+            const int ed = d == 0 ? ex : d == 1 ? ey : ez;
+            int jx, jy, jz;
+            face_site(d, f, high ? ed - 1 : 0, jx, jy, jz);
+            v = site_xyz(jx, jy, jz, d, high ? 1 : -1);
+        }
+        slot_xyz[sl] = v;
+    }
+    __syncthreads();
+    // copy the field of slice t into buffer buf (asynchronous)
+    auto stage = [&](int t, int buf) {
+        float* dst = XO + buf * kLcSlots * kLcRow;
+        for (int idx = tid; idx < kLcSlots * 8; idx += kLcThreads) {
+            const int sl = idx >> 3, c = idx & 7;
+            const int v = slot_xyz[sl];
+            if (v >= 0) cp_async16(dst + sl * kLcRow + c * 4, X + ((size_t)v + (size_t)t * slice) * 32 + c * 4);
+        }
+    };
+    // this thread's site (dead threads of a partial box compute on site 0 and store nothing)
+    const bool live = s < nsite;
+    const int sx = live ? s : 0;
+    const int ix = sx % ex, iy = (sx / ex) % ey, iz = sx / (ex * ey);
+    const int xyz = slot_xyz[sx];
+    // slot of the forward neighbour along d < 3, and whether it is a box site (its B lands in this box)
+    int nb_slot = 0, tgt_local = -1;
+    if (nu < 3) {
+        const int ed = nu == 0 ? ex : nu == 1 ? ey : ez;
+        const bool fd = nu == 0 ? fx : nu == 1 ? fy : fz;
+        const int id = nu == 0 ? ix : nu == 1 ? iy : iz;
+        if (id + 1 < ed || fd) {
+            const int jx = nu == 0 ? (id + 1 < ed ? ix + 1 : 0) : ix;
+            const int jy = nu == 1 ? (id + 1 < ed ? iy + 1 : 0) : iy;
+            const int jz = nu == 2 ? (id + 1 < ed ? iz + 1 : 0) : iz;
+            tgt_local = jx + ex * (jy + ey * jz);
+            nb_slot = tgt_local;
+        } else {
+            const int off = nu == 0 ? 0 : nu == 1 ? hx : hx + hy;
+            const int f = nu == 0 ? iy + ey * iz : nu == 1 ? ix + ex * iz : ix + ex * iy;
+            nb_slot = hiB + off + f;
+        }
+    }
+    // halo task of this thread: link hl of the low faces, component hmu
+    const bool has_halo = tid < 4 * nhalo;
+    int h_d = 0, h_local = 0, h_slot = 0, h_xyz = 0;
+    const int hmu = tid & 3;
+    if (has_halo) {
+        int f = tid >> 2;
+        h_slot = loB + f;
+        if (f >= hx) { f -= hx; h_d = 1; if (f >= hy) { f -= hy; h_d = 2; } }
+        int jx, jy, jz;
+        face_site(h_d, f, 0, jx, jy, jz);
+        h_local = jx + ex * (jy + ey * jz);
+        h_xyz = slot_xyz[h_slot];
+    }
+    // first slice: field (synchronous), t-halo B_t(x, t0 - 1) split by component, prefetched registers
+    stage(t0, t0 & 1);
+    {
+        const int tp = t0 == 0 ? Lt - 1 : t0 - 1;
+        const int m = nu;   // component of the t-halo task
+        const mat3<float> u = LinkLoad<float, LF>::load(U, xyz + tp * slice, 3);
+        float xm[8];
+        load8(X + ((size_t)xyz + (size_t)tp * slice) * 32 + m * 8, xm);
+        float Bm[8];
 #pragma unroll
-        for (int m = 0; m < 4; m++) load8(X + (size_t)lsite * 32 + m * 8, xo[m]);
-        float B[4][8];
+        for (int c = 0; c < 8; c++) Bm[c] = 0.f;
+        lc_rows(u, [&](int ra, const float (&row)[8]) {
+#pragma unroll
+            for (int c = 0; c < 8; c++) Bm[c] = fmaf(row[c], xm[ra], Bm[c]);
+        });
+        if (live) {
+            float4* q = reinterpret_cast<float4*>(BT + (size_t)((t0 & 1) * kLcSites + s) * kLcBT + m * 8);
+            q[0] = make_float4(Bm[0], Bm[1], Bm[2], Bm[3]);
+            q[1] = make_float4(Bm[4], Bm[5], Bm[6], Bm[7]);
+        }
+    }
+    mat3<float> u = LinkLoad<float, LF>::load(U, xyz + t0 * slice, nu);
+    mat3<float> uh;
+    if (has_halo) uh = LinkLoad<float, LF>::load(U, h_xyz + t0 * slice, h_d);
+    float xf[4][8];
+    if (nu == 3) {
+        const int tn = t0 + 1 == Lt ? 0 : t0 + 1;
+#pragma unroll
+        for (int m = 0; m < 4; m++) load8(X + ((size_t)xyz + (size_t)tn * slice) * 32 + m * 8, xf[m]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    float dot = 0.f;
+    for (int t = t0; t < t1; t++) {
+        const int cur = t & 1;
+        const float* XC = XO + cur * kLcSlots * kLcRow;
+        if (t + 1 < t1) stage(t + 1, cur ^ 1);
+        // ---- halo: B_d of the low-face links, component hmu
+        if (has_halo) {
+            float xm[8], Bm[8];
+            {
+                const float4* p = reinterpret_cast<const float4*>(XC + h_slot * kLcRow + hmu * 8);
+                const float4 v0 = p[0], v1 = p[1];
+                xm[0] = v0.x; xm[1] = v0.y; xm[2] = v0.z; xm[3] = v0.w; xm[4] = v1.x; xm[5] = v1.y; xm[6] = v1.z; xm[7] = v1.w;
+            }
+#pragma unroll
+            for (int c = 0; c < 8; c++) Bm[c] = 0.f;
+            lc_rows(uh, [&](int ra, const float (&row)[8]) {
+#pragma unroll
+                for (int c = 0; c < 8; c++) Bm[c] = fmaf(row[c], xm[ra], Bm[c]);
+            });
+            float4* q = reinterpret_cast<float4*>(BS + h_local * kLcBS + h_d * 32 + hmu * 8);
+            q[0] = make_float4(Bm[0], Bm[1], Bm[2], Bm[3]);
+            q[1] = make_float4(Bm[4], Bm[5], Bm[6], Bm[7]);
+        }
+        // ---- main: the link U_nu(x); forward rows summed over nu into Hs, backward B to the target slot
+        if (nu < 3) {
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                const float4* p = reinterpret_cast<const float4*>(XC + nb_slot * kLcRow + m * 8);
+                const float4 v0 = p[0], v1 = p[1];
+                xf[m][0] = v0.x; xf[m][1] = v0.y; xf[m][2] = v0.z; xf[m][3] = v0.w;
+                xf[m][4] = v1.x; xf[m][5] = v1.y; xf[m][6] = v1.z; xf[m][7] = v1.w;
+            }
+        }
+        float B[4][8], Hs[8];
 #pragma unroll
         for (int m = 0; m < 4; m++)
 #pragma unroll
             for (int c = 0; c < 8; c++) B[m][c] = 0.f;
+        const float* xo = XC + sx * kLcRow;
         lc_rows(u, [&](int ra, const float (&row)[8]) {
+            float f[4];
 #pragma unroll
-            for (int m = 0; m < 4; m++)
+            for (int m = 0; m < 4; m++) {
+                float v = 0.f;
 #pragma unroll
-                for (int c = 0; c < 8; c++) B[m][c] = fmaf(row[c], xo[m][ra], B[m][c]);
+                for (int c = 0; c < 8; c++) v = fmaf(row[c], xf[m][c], v);
+                f[m] = v;
+            }
+            Hs[ra] = quad_transpose_sum(f, nu);
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                const float xm = xo[m * 8 + ra];
+#pragma unroll
+                for (int c = 0; c < 8; c++) B[m][c] = fmaf(row[c], xm, B[m][c]);
+            }
         });
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            float4* q = reinterpret_cast<float4*>(dst + m * 8);
-            q[0] = make_float4(B[m][0], B[m][1], B[m][2], B[m][3]);
-            q[1] = make_float4(B[m][4], B[m][5], B[m][6], B[m][7]);
+        float* dst = nullptr;
+        if (live) {
+            if (nu == 3) dst = BT + (size_t)((cur ^ 1) * kLcSites + s) * kLcBT;
+            else if (tgt_local >= 0) dst = BS + tgt_local * kLcBS + nu * 32;
         }
-    };
-    float dot = 0.f;
-    int cur = 0;
-    // t-halo: B_t of the links U_t(x, t0 - 1) for the first slice
-    if (nu == 0 && live) {
-        const int tp = t0 == 0 ? g.L[3] - 1 : t0 - 1;
-        backward_only(xyz + tp * slice, 3, BT + (size_t)s * kLcBT);
-    }
-    for (int t = t0; t < t1; t++) {
+        if (dst) {
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                float4* q = reinterpret_cast<float4*>(dst + m * 8);
+                q[0] = make_float4(B[m][0], B[m][1], B[m][2], B[m][3]);
+                q[1] = make_float4(B[m][4], B[m][5], B[m][6], B[m][7]);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        // ---- epilogue for component mu = nu; the next slice's links (and X(x, t+2) for nu = t) are loaded first
         const int x = xyz + t * slice;
-        // own field, transposed: XO[s][a * 4 + mu]
-        if (live) {
-            float v[8];
-            load8(X + (size_t)x * 32 + nu * 8, v);
-#pragma unroll
-            for (int c = 0; c < 8; c++) XO[s * kLcXO + c * 4 + nu] = v[c];
-        }
-        __syncthreads();
-        if (live) {
-            // the link U_nu(x) and the field one step forward
-            const int xf_site = nu < 3 ? fwd_xyz(nu) + t * slice : xyz + (t + 1 == g.L[3] ? 0 : t + 1) * slice;
-            const mat3<float> u = LinkLoad<float, LF>::load(U, x, nu);
-            float xf[4][8];
-#pragma unroll
-            for (int m = 0; m < 4; m++) load8(X + (size_t)xf_site * 32 + m * 8, xf[m]);
-            float B[4][8];
-#pragma unroll
-            for (int m = 0; m < 4; m++)
-#pragma unroll
-                for (int c = 0; c < 8; c++) B[m][c] = 0.f;
-            float* fs_out = FS + s * kLcFS + nu;
-            const float* xo = XO + s * kLcXO;
-            lc_rows(u, [&](int ra, const float (&row)[8]) {
-                // forward row ra: F[mu][ra] = row . X(x+nu)_mu
-#pragma unroll
-                for (int m = 0; m < 4; m++) {
-                    float f = 0.f;
-#pragma unroll
-                    for (int c = 0; c < 8; c++) f = fmaf(row[c], xf[m][c], f);
-                    fs_out[m * kLcFmu + ra * 4] = f;
-                }
-                // backward: B[mu][c] += Ad[ra][c] X(x)_mu[ra]
-                const float4 xq = *reinterpret_cast<const float4*>(xo + ra * 4);
-                const float xm[4] = {xq.x, xq.y, xq.z, xq.w};
-#pragma unroll
-                for (int m = 0; m < 4; m++)
-#pragma unroll
-                    for (int c = 0; c < 8; c++) B[m][c] = fmaf(row[c], xm[m], B[m][c]);
-            });
-            float* dst = nullptr;
+        float qo[8];
+        if (MODE == 1 && k > 0 && live) load8(Y + (size_t)x * 32 + nu * 8, qo);
+        if (t + 1 < t1) {
+            u = LinkLoad<float, LF>::load(U, xyz + (t + 1) * slice, nu);
+            if (has_halo) uh = LinkLoad<float, LF>::load(U, h_xyz + (t + 1) * slice, h_d);
             if (nu == 3) {
-                dst = BT + (size_t)((cur ^ 1) * kLcSites + s) * kLcBT;
-            } else {
-                const int tl = fwd_local(nu);
-                if (tl >= 0) dst = BS + tl * kLcBS + nu * 32;
-            }
-            if (dst) {
+                const int tn = t + 2 >= Lt ? t + 2 - Lt : t + 2;
 #pragma unroll
-                for (int m = 0; m < 4; m++) {
-                    float4* q = reinterpret_cast<float4*>(dst + m * 8);
-                    q[0] = make_float4(B[m][0], B[m][1], B[m][2], B[m][3]);
-                    q[1] = make_float4(B[m][4], B[m][5], B[m][6], B[m][7]);
-                }
+                for (int m = 0; m < 4; m++) load8(X + ((size_t)xyz + (size_t)tn * slice) * 32 + m * 8, xf[m]);
             }
         }
-        // halo: backward contributions into the box's low faces from links outside it
-        for (int h = tid; h < nhalo; h += kLcThreads) {
-            // face site (coordinate d = 0 in the box) and the lattice site one step below it along d
-            int d, jx, jy, jz;
-            if (h < hx) { d = 0; jx = 0; jy = h % ey; jz = h / ey; }
-            else if (h < hx + hy) { d = 1; const int r = h - hx; jy = 0; jx = r % ex; jz = r / ex; }
-            else { d = 2; const int r = h - hx - hy; jz = 0; jx = r % ex; jy = r / ex; }
-            const int ls = jx + ex * (jy + ey * jz);
-            int bx = c0x + jx, by = c0y + jy, bz = c0z + jz;
-            if (d == 0) bx = bx == 0 ? g.L[0] - 1 : bx - 1;
-            else if (d == 1) by = by == 0 ? g.L[1] - 1 : by - 1;
-            else bz = bz == 0 ? g.L[2] - 1 : bz - 1;
-            const int site = bx + g.L[0] * (by + g.L[1] * bz) + t * slice;
-            backward_only(site, d, BS + ls * kLcBS + d * 32);
-        }
-        __syncthreads();
-        // sum per (site, mu = nu) and the epilogue
         if (live) {
             const int m = nu;
-            float H[8];
-            const float* fr = FS + s * kLcFS + m * kLcFmu;
-#pragma unroll
-            for (int c = 0; c < 8; c++) {
-                const float4 q = *reinterpret_cast<const float4*>(fr + c * 4);
-                H[c] = (q.x + q.y) + (q.z + q.w);
-            }
             const float* bt = BT + (size_t)(cur * kLcSites + s) * kLcBT + m * 8;
             const float* b0 = BS + s * kLcBS + m * 8;
+            const float* xs = XC + s * kLcRow + m * 8;
+            float y[8];
 #pragma unroll
-            for (int c = 0; c < 8; c++) H[c] += ((b0[c] + b0[32 + c]) + b0[64 + c]) + bt[c];
-            float xo[8], y[8];
-#pragma unroll
-            for (int c = 0; c < 8; c++) xo[c] = XO[s * kLcXO + c * 4 + m];
-            float* out = Y + (size_t)x * 32 + m * 8;
-            if (MODE == 0) {
-#pragma unroll
-                for (int c = 0; c < 8; c++) y[c] = fmaf(b, H[c], a * xo[c]);
-            } else {
-                if (k > 0) {
-                    float qo[8];
-                    load8(out, qo);
-#pragma unroll
-                    for (int c = 0; c < 8; c++) y[c] = fmaf(beta, qo[c], fmaf(b, H[c], a * xo[c]));
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 8; c++) y[c] = fmaf(b, H[c], a * xo[c]);
-                }
-#pragma unroll
-                for (int c = 0; c < 8; c++) dot = fmaf(xo[c], y[c], dot);
+            for (int c = 0; c < 8; c++) {
+                const float h = Hs[c] + (((b0[c] + b0[32 + c]) + b0[64 + c]) + bt[c]);
+                y[c] = fmaf(b, h, a * xs[c]);
             }
-            store8(out, y);
+            if (MODE == 1) {
+                if (k > 0)
+#pragma unroll
+                    for (int c = 0; c < 8; c++) y[c] = fmaf(beta, qo[c], y[c]);
+#pragma unroll
+                for (int c = 0; c < 8; c++) dot = fmaf(xs[c], y[c], dot);
+            }
+            store8(Y + (size_t)x * 32 + m * 8, y);
         }
-        cur ^= 1;
         __syncthreads();
     }
     if (MODE == 1) {

@@ -131,3 +131,28 @@ def test_autograd_laplacian():
         (Y * dev(G)).sum().backward()
     assert rel_l2(host(Xd.grad), oracle.lap(L, U, G)) <= 1e-12
     assert rel_l2(host(omega.grad), oracle.lap_link_grad(L, U, X, G, [1.0])) <= 1e-12
+
+
+@pytest.mark.parametrize("L", [(8, 6, 4, 10), (16, 16, 16, 16)])
+def test_staged_contraction_matches_global(L):
+    """The kinetic force with the basis rows staged in shared memory equals the one reading them from global
+    memory (same arithmetic, different source), and both match the oracle's force; a tight tolerance makes
+    the Krylov run longer than the 20 staged rows, which takes the global reads inside the staged kernel."""
+    import paper_2112_04556_gb300 as rm
+    U = inputs.random_links(L, eps=0.4, seed=41)
+    P = inputs.gaussian_fields(L, 1, seed=42)[0]
+    m = fit.mass_term(12, 0.9)
+    out = {}
+    with rm.Context(L) as ctx:
+        Ud, Pd = dev(U), dev(P)
+        for staged in (1, 0):
+            rm.set_stencil_shape(ctx, rm.SHAPE_KFORCE, rm.FP32, 18, staged, 128)
+            for tol in (1e-6, 1e-9):
+                out[(staged, tol)] = host(rm.kinetic_force(ctx, Ud, Pd, m, tol=tol, prec=rm.MIXED)[0])
+        with pytest.raises(rm.RmhmcError):
+            rm.set_stencil_shape(ctx, rm.SHAPE_KFORCE, rm.FP32, 18, 2, 128)
+    for tol in (1e-6, 1e-9):
+        assert rel_l2(out[(1, tol)], out[(0, tol)]) <= 1e-6, tol
+    if np.prod(L) <= 4096:
+        _, ref, _ = oracle.kinetic(L, U, P, m, tol=1e-13)
+        assert rel_l2(out[(1, 1e-9)], ref) <= 1e-5
