@@ -318,9 +318,11 @@ struct rmhmc_ctx {
     std::string graph_note;
     // autotuned stencil shapes per (precision bytes * 100 + link format): components per lane, block size
     std::map<int, std::pair<int, int>> tune;
-    // kinetic-force contraction with the block's own basis rows staged in shared memory (rmhmc_set_stencil_shape;
-    // off by default: at 32^4 the staged kernel's two resident blocks per SM made a kinetic evaluation 1.4 ms slower)
-    bool lg_staged = false;
+    // kernel of the kinetic-force contraction (rmhmc_set_stencil_shape, RMHMC_SHAPE_KFORCE): 0 four lanes per link,
+    // own basis rows from global memory; 1 the same with the rows staged in shared memory; 2 eight lanes per link
+    int lg_mode = 2;
+    // float64 link update in float-float arithmetic (rmhmc_set_stencil_shape, RMHMC_SHAPE_LINKUPDATE)
+    bool link_update_ff = true;
     std::string tune_report;
     // counters: kernels launched; optional timing of the conjugate-gradient stencil launches
     long long launches = 0;

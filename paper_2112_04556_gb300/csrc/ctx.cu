@@ -228,10 +228,16 @@ extern "C" int rmhmc_tuning(const rmhmc_ctx* ctx, char* buf, int len) {
 extern "C" int rmhmc_set_stencil_shape(rmhmc_ctx* ctx, int kernel, int prec, int linkfmt, int nmu, int block) {
     if (!ctx) return RMHMC_EINVAL;
     ctx->err.clear();
+    if (kernel == RMHMC_SHAPE_LINKUPDATE) {
+        if (prec != RMHMC_FP64 || linkfmt != 18 || (nmu != 0 && nmu != 1) || block != 128)
+            return set_err(ctx, RMHMC_EINVAL, "link update: RMHMC_FP64, 18, nmu 0 or 1, block 128");
+        ctx->link_update_ff = nmu == 1;
+        return RMHMC_OK;
+    }
     if (kernel == RMHMC_SHAPE_KFORCE) {
-        if (prec != RMHMC_FP32 || linkfmt != 18 || (nmu != 0 && nmu != 1) || block != 128)
-            return set_err(ctx, RMHMC_EINVAL, "kinetic-force contraction: RMHMC_FP32, 18, nmu 0 or 1, block 128");
-        ctx->lg_staged = nmu == 1;
+        if (prec != RMHMC_FP32 || linkfmt != 18 || nmu < 0 || nmu > 2 || block != (nmu == 2 ? 256 : 128))
+            return set_err(ctx, RMHMC_EINVAL, "kinetic-force contraction: RMHMC_FP32, 18, nmu 0/1 with block 128 or 2 with 256");
+        ctx->lg_mode = nmu;
         return RMHMC_OK;
     }
     if (kernel != RMHMC_SHAPE_LAP && kernel != RMHMC_SHAPE_CG) return set_err(ctx, RMHMC_EINVAL, "bad kernel");

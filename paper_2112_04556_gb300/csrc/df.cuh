@@ -1,0 +1,78 @@
+// Float-float ("double-float") arithmetic: a value is an unevaluated sum hi + lo of two float32 numbers with
+// |lo| <= ulp(hi)/2, about 48 significant bits.  Built from the error-free transformations of Knuth's TwoSum
+// (TAOCP vol. 2, 4.2.2) and the FMA form of Dekker's TwoProduct (Dekker 1971): every rounding error of a sum or
+// product is recovered exactly and carried in lo.  All operations use the _rn intrinsics, so the compiler
+// cannot contract or reassociate them.  On GB300 float64 runs at 1/62 of the float32 rate; a float-float
+// product or sum costs 4 to 20 float32 operations, so float64-accurate link updates are several times cheaper
+// this way.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace rm {
+
+struct dfl { float hi, lo; };
+struct cdfl { dfl re, im; };
+
+__device__ __forceinline__ dfl df_make(float h, float l) { dfl r; r.hi = h; r.lo = l; return r; }
+__device__ __forceinline__ dfl df_from(double x) {
+    const float h = __double2float_rn(x);
+    return df_make(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
+
+// s + e = a + b exactly (TwoSum)
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df_make(s, e);
+}
+// the same when |a| >= |b|
+__device__ __forceinline__ dfl quick_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+    dfl s = two_sum(a.hi, b.hi);
+    const dfl t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return df_make(-a.hi, -a.lo); }
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ dfl df_mulf(dfl a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ dfl df_zero() { return df_make(0.f, 0.f); }
+
+__device__ __forceinline__ cdfl cdf_make(dfl re, dfl im) { cdfl r; r.re = re; r.im = im; return r; }
+__device__ __forceinline__ cdfl cdf_add(cdfl a, cdfl b) { return cdf_make(df_add(a.re, b.re), df_add(a.im, b.im)); }
+__device__ __forceinline__ cdfl cdf_sub(cdfl a, cdfl b) { return cdf_make(df_sub(a.re, b.re), df_sub(a.im, b.im)); }
+__device__ __forceinline__ cdfl cdf_conj(cdfl a) { return cdf_make(a.re, df_neg(a.im)); }
+__device__ __forceinline__ cdfl cdf_mul(cdfl a, cdfl b) {
+    return cdf_make(df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re)));
+}
+__device__ __forceinline__ cdfl cdf_scale(cdfl a, dfl s) { return cdf_make(df_mul(a.re, s), df_mul(a.im, s)); }
+// |a|^2
+__device__ __forceinline__ dfl cdf_norm(cdfl a) { return df_add(df_mul(a.re, a.re), df_mul(a.im, a.im)); }
+
+// 1/sqrt(a) for a > 0: float32 estimate, then one Newton step y + y (1 - a y^2) / 2 in float-float
+__device__ __forceinline__ dfl df_rsqrt(dfl a) {
+    const dfl y = df_make(rsqrtf(a.hi), 0.f);
+    const dfl r = df_sub(df_make(1.f, 0.f), df_mul(a, df_mul(y, y)));
+    return df_add(y, df_mul(y, df_mulf(r, 0.5f)));
+}
+
+}  // namespace rm

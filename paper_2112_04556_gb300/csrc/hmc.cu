@@ -15,6 +15,7 @@
 
 #include <algorithm>
 
+#include "df.cuh"
 #include "krylov.cuh"
 #include "ops.cuh"
 #include "philox.cuh"
@@ -196,6 +197,193 @@ __global__ void __launch_bounds__(kBlock) k_link_update(const double* __restrict
             u32a[(size_t)(mu * 3 + 2) * nsite + s] = make_float4(R.e[1][1].re, R.e[1][1].im, R.e[1][2].re, R.e[1][2].im);
 #pragma unroll
             for (int j = 0; j < 3; j++) u32b[(size_t)(mu * 3 + j) * nsite + s] = make_float2(R.e[2][j].re, R.e[2][j].im);
+        }
+    }
+    if (maxdiff) {
+        __shared__ double sh[kBlock / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) diff = fmax(diff, __shfl_down_sync(0xffffffffu, diff, o));
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = diff;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = 0.0;
+            for (int w = 0; w < kBlock / 32; w++) m = fmax(m, sh[w]);
+            atomic_max_nonneg(maxdiff, m);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// The same update in float-float arithmetic (df.cuh): exp(i Q) by the Cayley-Hamilton power series (the
+// branch expi takes for c1 = Tr Q^2 / 2 < 1/4, which covers every MD step), the product with U and the
+// reunitarisation, all to ~2^-48 relative, at a fraction of the float64 cost.  Links with c1 >= 0.24 (a
+// rotation by more than about half a radian) take the float64 path of k_link_update.
+// ------------------------------------------------------------------------------------------------
+__constant__ double kInvFactorial[26] = {
+    1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040, 1.0 / 40320, 1.0 / 362880,
+    1.0 / 3628800.0, 1.0 / 39916800.0, 1.0 / 479001600.0, 1.0 / 6227020800.0, 1.0 / 87178291200.0,
+    1.0 / 1307674368000.0, 1.0 / 20922789888000.0, 1.0 / 355687428096000.0, 1.0 / 6402373705728000.0,
+    1.0 / 121645100408832000.0, 1.0 / 2432902008176640000.0, 1.0 / 51090942171709440000.0,
+    1.0 / 1124000727777607680000.0, 1.0 / 25852016738884976640000.0, 1.0 / 620448401733239439360000.0,
+    1.0 / 15511210043330985984000000.0};
+
+struct hermdf { dfl d[3]; cdfl o[3]; };   // d: diagonal, o: 01, 02, 12
+
+__device__ __forceinline__ cdfl hdf_entry(const hermdf& h, int i, int j) {
+    if (i == j) return cdf_make(h.d[i], df_zero());
+    const int lo = i < j ? i : j, hi = i < j ? j : i;
+    const int idx = lo == 0 ? (hi == 1 ? 0 : 1) : 2;
+    return i < j ? h.o[idx] : cdf_conj(h.o[idx]);
+}
+
+// R = exp(i Q) U in float-float, Q = eps V (V: 8 float64 coefficients), optionally reunitarised
+__device__ __forceinline__ void link_update_df(const double (&v)[8], double eps, const mat3<double>& U, bool reunit,
+                                               cdfl (&R)[3][3]) {
+    // Q = eps sum_a v_a T^a: diagonal (v3 + v8/sqrt3, -v3 + v8/sqrt3, -2 v8/sqrt3)/2, off-diagonal (v1 - i v2)/2, ...
+    const double r3 = 0.57735026918962576451;
+    hermdf Q;
+    Q.d[0] = df_from(0.5 * eps * (v[2] + v[7] * r3));
+    Q.d[1] = df_from(0.5 * eps * (-v[2] + v[7] * r3));
+    Q.d[2] = df_from(-eps * v[7] * r3);
+    Q.o[0] = cdf_make(df_from(0.5 * eps * v[0]), df_from(-0.5 * eps * v[1]));
+    Q.o[1] = cdf_make(df_from(0.5 * eps * v[3]), df_from(-0.5 * eps * v[4]));
+    Q.o[2] = cdf_make(df_from(0.5 * eps * v[5]), df_from(-0.5 * eps * v[6]));
+    // Q^2 (Hermitian), c1 = Tr Q^2 / 2, c0 = det Q
+    const dfl n01 = cdf_norm(Q.o[0]), n02 = cdf_norm(Q.o[1]), n12 = cdf_norm(Q.o[2]);
+    hermdf Q2;
+    Q2.d[0] = df_add(df_mul(Q.d[0], Q.d[0]), df_add(n01, n02));
+    Q2.d[1] = df_add(df_mul(Q.d[1], Q.d[1]), df_add(n01, n12));
+    Q2.d[2] = df_add(df_mul(Q.d[2], Q.d[2]), df_add(n02, n12));
+    Q2.o[0] = cdf_add(cdf_scale(Q.o[0], df_add(Q.d[0], Q.d[1])), cdf_mul(Q.o[1], cdf_conj(Q.o[2])));
+    Q2.o[1] = cdf_add(cdf_scale(Q.o[1], df_add(Q.d[0], Q.d[2])), cdf_mul(Q.o[0], Q.o[2]));
+    Q2.o[2] = cdf_add(cdf_scale(Q.o[2], df_add(Q.d[1], Q.d[2])), cdf_mul(cdf_conj(Q.o[0]), Q.o[1]));
+    const dfl c1 = df_mulf(df_add(df_add(Q2.d[0], Q2.d[1]), Q2.d[2]), 0.5f);
+    const cdfl t = cdf_mul(Q.o[0], Q.o[2]);   // Q01 Q12; Q01 Q12 Q20 = t conj(Q02)
+    dfl c0 = df_mul(df_mul(Q.d[0], Q.d[1]), Q.d[2]);
+    c0 = df_add(c0, df_mulf(df_add(df_mul(t.re, Q.o[1].re), df_mul(t.im, Q.o[1].im)), 2.f));
+    c0 = df_sub(c0, df_add(df_add(df_mul(Q.d[0], n12), df_mul(Q.d[1], n02)), df_mul(Q.d[2], n01)));
+    // f_k = sum_n (i^n / n!) {a_n, b_n, c_n}_k, Q^n = a_n + b_n Q + c_n Q^2, Q^3 = c1 Q + c0
+    dfl fr[3] = {df_zero(), df_zero(), df_zero()}, fi[3] = {df_zero(), df_zero(), df_zero()};
+    dfl a = df_make(1.f, 0.f), b = df_zero(), c = df_zero();
+    for (int n = 0; n < 26; n++) {
+        const dfl inv = df_from(kInvFactorial[n]);
+        const dfl sa = df_mul(inv, a), sb = df_mul(inv, b), sc = df_mul(inv, c);
+        const int ph = n & 3;   // i^n = 1, i, -1, -i
+        if (ph == 0) { fr[0] = df_add(fr[0], sa); fr[1] = df_add(fr[1], sb); fr[2] = df_add(fr[2], sc); }
+        else if (ph == 1) { fi[0] = df_add(fi[0], sa); fi[1] = df_add(fi[1], sb); fi[2] = df_add(fi[2], sc); }
+        else if (ph == 2) { fr[0] = df_sub(fr[0], sa); fr[1] = df_sub(fr[1], sb); fr[2] = df_sub(fr[2], sc); }
+        else { fi[0] = df_sub(fi[0], sa); fi[1] = df_sub(fi[1], sb); fi[2] = df_sub(fi[2], sc); }
+        if (n >= 3 && fabsf(sa.hi) + fabsf(sb.hi) + fabsf(sc.hi) < 1e-18f) break;
+        const dfl an = df_mul(c0, c), bn = df_add(df_mul(c1, c), a);
+        c = b; a = an; b = bn;
+    }
+    const cdfl f0 = cdf_make(fr[0], fi[0]), f1 = cdf_make(fr[1], fi[1]), f2 = cdf_make(fr[2], fi[2]);
+    // E = f0 + f1 Q + f2 Q^2, R = E U
+    cdfl E[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            cdfl e = cdf_add(cdf_mul(f1, hdf_entry(Q, i, j)), cdf_mul(f2, hdf_entry(Q2, i, j)));
+            if (i == j) e = cdf_add(e, f0);
+            E[i][j] = e;
+        }
+    cdfl Ud[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) Ud[i][j] = cdf_make(df_from(U.e[i][j].re), df_from(U.e[i][j].im));
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            cdfl s = cdf_mul(E[i][0], Ud[0][j]);
+            s = cdf_add(s, cdf_mul(E[i][1], Ud[1][j]));
+            s = cdf_add(s, cdf_mul(E[i][2], Ud[2][j]));
+            R[i][j] = s;
+        }
+    if (!reunit) return;
+    // Gram-Schmidt on the first two rows, third row = conj(row0 x row1)
+    dfl nn = df_add(df_add(cdf_norm(R[0][0]), cdf_norm(R[0][1])), cdf_norm(R[0][2]));
+    dfl sc0 = df_rsqrt(nn);
+#pragma unroll
+    for (int j = 0; j < 3; j++) R[0][j] = cdf_scale(R[0][j], sc0);
+    cdfl p = cdf_make(df_zero(), df_zero());   // <row0, row1>
+#pragma unroll
+    for (int j = 0; j < 3; j++) p = cdf_add(p, cdf_mul(cdf_conj(R[0][j]), R[1][j]));
+#pragma unroll
+    for (int j = 0; j < 3; j++) R[1][j] = cdf_sub(R[1][j], cdf_mul(p, R[0][j]));
+    nn = df_add(df_add(cdf_norm(R[1][0]), cdf_norm(R[1][1])), cdf_norm(R[1][2]));
+    sc0 = df_rsqrt(nn);
+#pragma unroll
+    for (int j = 0; j < 3; j++) R[1][j] = cdf_scale(R[1][j], sc0);
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        R[2][j] = cdf_conj(cdf_sub(cdf_mul(R[0][j1], R[1][j2]), cdf_mul(R[0][j2], R[1][j1])));
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_link_update_ff(const double* __restrict__ Uin, const double* __restrict__ V,
+                                                           double eps, int reunit, double* __restrict__ Uout,
+                                                           const double* __restrict__ Wold, double* maxdiff,
+                                                           double2* u64, float4* u32a, float2* u32b, int nsite) {
+    const int lk = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = lk >> 2, mu = lk & 3;
+    double diff = 0.0;
+    if (s < nsite) {
+        const size_t l = (size_t)s * 4 + mu;
+        double v[8];
+        load8(V + l * 8, v);
+        mat3<double> U;
+        const double2* src = reinterpret_cast<const double2*>(Uin + l * 18);
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) { const double2 z = src[3 * i + j]; U.e[i][j] = cmk(z.x, z.y); }
+        // c1 = Tr Q^2 / 2 = eps^2 |v|^2 / 4 decides the branch
+        float vv = 0.f;
+#pragma unroll
+        for (int a = 0; a < 8; a++) vv = fmaf((float)v[a], (float)v[a], vv);
+        const float c1 = 0.25f * (float)(eps * eps) * vv;
+        mat3<double> Rd;
+        if (c1 < 0.24f) {
+            cdfl R[3][3];
+            link_update_df(v, eps, U, reunit != 0, R);
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) Rd.e[i][j] = cmk(df_to(R[i][j].re), df_to(R[i][j].im));
+        } else {
+            double w[8];
+#pragma unroll
+            for (int a = 0; a < 8; a++) w[a] = v[a] * eps;
+            herm<double> Q = coef_to_herm2(w);
+#pragma unroll
+            for (int k = 0; k < 3; k++) { Q.d[k] *= 0.5; Q.o[k] = cscale(Q.o[k], 0.5); }
+            Rd = m_mul(expi<double>(Q), U);
+            if (reunit) reunitarise(Rd);
+        }
+        double2* dst = reinterpret_cast<double2*>(Uout + l * 18);
+        const double2* old = Wold ? reinterpret_cast<const double2*>(Wold + l * 18) : nullptr;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const double2 z = make_double2(Rd.e[i][j].re, Rd.e[i][j].im);
+                if (old) {
+                    const double2 o = old[3 * i + j];
+                    diff = fmax(diff, fmax(fabs(z.x - o.x), fabs(z.y - o.y)));
+                }
+                dst[3 * i + j] = z;
+                if (u64) u64[(size_t)(mu * 9 + 3 * i + j) * nsite + s] = z;
+            }
+        if (u32a) {
+            u32a[(size_t)(mu * 3 + 0) * nsite + s] = make_float4(Rd.e[0][0].re, Rd.e[0][0].im, Rd.e[0][1].re, Rd.e[0][1].im);
+            u32a[(size_t)(mu * 3 + 1) * nsite + s] = make_float4(Rd.e[0][2].re, Rd.e[0][2].im, Rd.e[1][0].re, Rd.e[1][0].im);
+            u32a[(size_t)(mu * 3 + 2) * nsite + s] = make_float4(Rd.e[1][1].re, Rd.e[1][1].im, Rd.e[1][2].re, Rd.e[1][2].im);
+#pragma unroll
+            for (int j = 0; j < 3; j++) u32b[(size_t)(mu * 3 + j) * nsite + s] = make_float2(Rd.e[2][j].re, Rd.e[2][j].im);
         }
     }
     if (maxdiff) {
@@ -457,8 +645,14 @@ __global__ void k_gauss_field(double* __restrict__ out, int V, uint64_t seed, ui
 int link_update_launch(rmhmc_ctx* ctx, const double* Uin, const double* V, double eps, bool reunit, double* Uout,
                        const double* Wold, double* dmax, bool internal, cudaStream_t st) {
     const int grid = lane_blocks(ctx);   // 4 V threads
-    k_link_update<<<grid, kBlock, 0, st>>>(Uin, V, eps, reunit ? 1 : 0, Uout, Wold, dmax, internal ? ctx->u64 : nullptr,
-                                           internal ? ctx->u32a : nullptr, internal ? ctx->u32b : nullptr, ctx->g.V); ++ctx->launches;
+    if (ctx->link_update_ff)
+        k_link_update_ff<<<grid, kBlock, 0, st>>>(Uin, V, eps, reunit ? 1 : 0, Uout, Wold, dmax,
+                                                  internal ? ctx->u64 : nullptr, internal ? ctx->u32a : nullptr,
+                                                  internal ? ctx->u32b : nullptr, ctx->g.V);
+    else
+        k_link_update<<<grid, kBlock, 0, st>>>(Uin, V, eps, reunit ? 1 : 0, Uout, Wold, dmax, internal ? ctx->u64 : nullptr,
+                                               internal ? ctx->u32a : nullptr, internal ? ctx->u32b : nullptr, ctx->g.V);
+    ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     if (internal) {
         ctx->links_valid = true;

@@ -370,6 +370,122 @@ __global__ void __launch_bounds__(kLgSites * 4, 2) k_link_grad_staged(Geom g, Li
     }
 }
 
+// The same contraction with eight lanes per link pair: the two halves of each (site, direction) split the rows b
+// of C (C[b][d], b = 4 h + i), so that a lane holds 32 accumulators instead of 64 and chunks of 8 basis vectors
+// (instead of 4) halve the passes over the site's own basis rows.  The half h is uniform per warp (threads
+// 0..127: h = 0, 128..255: h = 1), so no branch on it diverges; the two halves' force contributions meet in
+// shared memory in a fixed order.  The conjugation by the link uses the adjoint matrix (the lane's four
+// columns of Ad(U_nu(y))).
+constexpr int kLsSites = 32;             // sites per block: 4 directions x 2 halves = 8 lanes each
+constexpr int kLsKC = 8;                 // basis vectors per chunk of W
+constexpr int kLsPad = kLsKC * 32 + 4;   // W per site: [kk][mu][8] + 4
+
+template <int LF>
+__global__ void __launch_bounds__(kLsSites * 8, 2) k_link_grad_split(Geom g, Links32 U, const float* __restrict__ R,
+                                                                     size_t fs, const int* __restrict__ flags, int n,
+                                                                     const double* __restrict__ S, int ld,
+                                                                     double* __restrict__ G) {
+    __shared__ __align__(16) float Ws[kLsSites * kLsPad];
+    __shared__ float Ss[kLsKC * kBasisCap];
+    __shared__ float Gh[kLsSites * 4 * 8];   // the h = 1 halves' contributions
+    if (flags) n = flags[1];
+    const int h = threadIdx.x >> 7, sl = (threadIdx.x & 127) >> 2, nu = threadIdx.x & 3;
+    float* const wrow = Ws + sl * kLsPad;
+    for (int base = blockIdx.x * kLsSites; base < g.V; base += gridDim.x * kLsSites) {
+        const int y = base + sl;
+        const bool live = y < g.V;
+        const int yn = live ? step_site(g, y, nu, 1) : 0;
+        float C[4][8];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int d = 0; d < 8; d++) C[i][d] = 0.f;
+        for (int k0 = 0; k0 < n; k0 += kLsKC) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < kLsKC * n; t += blockDim.x) {
+                const int kk = t / n, l = t - kk * n;
+                Ss[kk * kBasisCap + l] = k0 + kk < n ? (float)S[(size_t)(k0 + kk) * ld + l] : 0.f;
+            }
+            __syncthreads();
+            // W_k,mu(y) = sum_l S_kl r_l,mu(y) for this half's four k of the chunk (mu = nu)
+            float w[4][8];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int a = 0; a < 8; a++) w[i][a] = 0.f;
+            if (live) {
+                for (int l = 0; l < n; l++) {
+                    float r[8];
+                    load8_v8(R + (size_t)l * fs + (size_t)y * 32 + nu * 8, r);
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        const float sv = Ss[(4 * h + i) * kBasisCap + l];
+#pragma unroll
+                        for (int a = 0; a < 8; a++) w[i][a] = fmaf(sv, r[a], w[i][a]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++) store8(wrow + (4 * h + i) * 32 + nu * 8, w[i]);
+            __syncthreads();
+            // C[b][d] += r_k,mu(y+nu)[b] W_k,mu(y)[d] for the rows b = 4 h + i
+            if (live) {
+                const int kc = min(kLsKC, n - k0);
+                for (int kk = 0; kk < kc; kk++) {
+                    const float* rk = R + (size_t)(k0 + kk) * fs + (size_t)yn * 32 + 4 * h;
+#pragma unroll
+                    for (int mu = 0; mu < 4; mu++) {
+                        const float4 rp = __ldg(reinterpret_cast<const float4*>(rk + mu * 8));
+                        float wv[8];
+                        lds8(wrow + kk * 32 + mu * 8, wv);
+                        const float rb[4] = {rp.x, rp.y, rp.z, rp.w};
+#pragma unroll
+                        for (int i = 0; i < 4; i++)
+#pragma unroll
+                            for (int d = 0; d < 8; d++) C[i][d] = fmaf(rb[i], wv[d], C[i][d]);
+                    }
+                }
+            }
+        }
+        // G^a = (1/16) sum_cd f_acd (Ad C)_cd; this half contributes the columns b = 4 h + i of Ad
+        float Gk[8];
+#pragma unroll
+        for (int a = 0; a < 8; a++) Gk[a] = 0.f;
+        if (live) {
+            const mat3<float> u = LinkLoad<float, LF>::load(U, y, nu);
+            float cols[4][8];
+            adjoint_columns(u, [&](int bcol, const float (&col)[8]) {
+                if ((bcol >> 2) == h)
+#pragma unroll
+                    for (int c = 0; c < 8; c++) cols[bcol & 3][c] = col[c];
+            });
+#pragma unroll
+            for (int d = 0; d < 8; d++) {
+                float rc[8];
+#pragma unroll
+                for (int c = 0; c < 8; c++) {
+                    float v = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 4; i++) v = fmaf(cols[i][c], C[i][d], v);
+                    rc[c] = v;
+                }
+                f_contract(d, rc, Gk);
+            }
+        }
+        if (h == 1) {
+#pragma unroll
+            for (int a = 0; a < 8; a++) Gh[(sl * 4 + nu) * 8 + a] = Gk[a];
+        }
+        __syncthreads();
+        if (h == 0 && live) {
+            double* out = G + (size_t)y * 32 + nu * 8;
+#pragma unroll
+            for (int a = 0; a < 8; a++) out[a] = (double)(Gk[a] + Gh[(sl * 4 + nu) * 8 + a]) * (1.0 / 16.0);
+        }
+        __syncthreads();   // Gh is rewritten by the next tile
+    }
+}
+
 // F_K from the basis rows (X_j rows 0..ns-1, Z_j rows ns..2ns-1, row stride ldr, device float64) of the
 // float32 basis R; n on the host, or read on the device from flags[1] when flags is given
 int link_grad_krylov_launch(rmhmc_ctx* ctx, const float* R, const double* rows, int ldr, int ns, const double* alpha,
@@ -382,7 +498,12 @@ int link_grad_krylov_launch(rmhmc_ctx* ctx, const float* R, const double* rows, 
     for (int j = 0; j < ns; j++) pw.w[j] = alpha[j];
     k_pair_matrix<<<ctx->num_sms / 4 > 1 ? ctx->num_sms / 4 : 1, 256, 0, st>>>(rows, ldr, ns, pw, flags, n, S, kBasisCap);
     ++ctx->launches;
-    if (ctx->lg_staged) {
+    if (ctx->lg_mode == 2) {
+        const int ntile = (ctx->g.V + kLsSites - 1) / kLsSites;
+        const int grid = std::max(1, std::min(ntile, (int)ctx->num_sms * 2));
+        k_link_grad_split<18><<<grid, kLsSites * 8, 0, st>>>(ctx->g, links32(ctx), R, field_elems(ctx), flags, n, S,
+                                                             kBasisCap, F);
+    } else if (ctx->lg_mode == 1) {
         static bool configured[64] = {};
         if (ctx->device < 0 || ctx->device >= 64) return set_err(ctx, RMHMC_EINVAL, "device index too large");
         if (!configured[ctx->device]) {

@@ -34,6 +34,30 @@ def test_link_update_matches_oracle(eps):
         assert np.abs(out2 - ref).max() <= 1e-13
 
 
+@pytest.mark.parametrize("eps", [1e-3, 0.05, 0.2, 0.7])
+def test_link_update_float_float_and_float64(eps):
+    """The float-float link update (the default) and the float64 one both match the oracle to 1e-13 and each
+    other to 1e-14, with and without reunitarisation; at eps = 0.7 most links rotate far enough to take the
+    float64 branch inside the float-float kernel."""
+    import paper_2112_04556_gb300 as rm
+    L = (6, 4, 4, 5)
+    U = inputs.random_links(L, eps=0.5, seed=52)
+    V = inputs.gaussian_fields(L, 1, seed=53)[0]
+    ref = oracle.link_update(L, U, V, eps)
+    out = {}
+    with rm.Context(L) as ctx:
+        for mode in (1, 0):
+            rm.set_stencil_shape(ctx, rm.SHAPE_LINKUPDATE, rm.FP64, 18, mode, 128)
+            for reunit in (False, True):
+                out[(mode, reunit)] = host(rm.link_update(ctx, dev(U), dev(V), eps, reunit=reunit))
+        with pytest.raises(rm.RmhmcError):
+            rm.set_stencil_shape(ctx, rm.SHAPE_LINKUPDATE, rm.FP32, 18, 1, 128)
+    for key, o in out.items():
+        assert np.abs(o - ref).max() <= 1e-13, key
+    for reunit in (False, True):
+        assert np.abs(out[(1, reunit)] - out[(0, reunit)]).max() <= 1e-14
+
+
 def _params(rm, mass, **kw):
     d = dict(beta=6.0, c1=0.0, mass=mass, tau=0.2, nsteps=4, tol_md=1e-13, tol_h=1e-13, fp_tol=1e-13,
              fp_maxit=100, maxiter=2000, prec=rm.FP64, seed=3, traj_index=0, metropolis=True)

@@ -135,9 +135,10 @@ def test_autograd_laplacian():
 
 @pytest.mark.parametrize("L", [(8, 6, 4, 10), (16, 16, 16, 16)])
 def test_staged_contraction_matches_global(L):
-    """The kinetic force with the basis rows staged in shared memory equals the one reading them from global
-    memory (same arithmetic, different source), and both match the oracle's force; a tight tolerance makes
-    the Krylov run longer than the 20 staged rows, which takes the global reads inside the staged kernel."""
+    """The three kernels of the kinetic force's basis contraction (four lanes per link reading the own basis rows
+    from global memory, the same with the rows staged in shared memory, eight lanes per link splitting the
+    accumulator) agree to float32 rounding and match the oracle's force; a tight tolerance makes the Krylov run
+    longer than the 20 staged rows, which takes the global reads inside the staged kernel."""
     import paper_2112_04556_gb300 as rm
     U = inputs.random_links(L, eps=0.4, seed=41)
     P = inputs.gaussian_fields(L, 1, seed=42)[0]
@@ -145,14 +146,17 @@ def test_staged_contraction_matches_global(L):
     out = {}
     with rm.Context(L) as ctx:
         Ud, Pd = dev(U), dev(P)
-        for staged in (1, 0):
-            rm.set_stencil_shape(ctx, rm.SHAPE_KFORCE, rm.FP32, 18, staged, 128)
+        for mode, block in ((1, 128), (0, 128), (2, 256)):
+            rm.set_stencil_shape(ctx, rm.SHAPE_KFORCE, rm.FP32, 18, mode, block)
             for tol in (1e-6, 1e-9):
-                out[(staged, tol)] = host(rm.kinetic_force(ctx, Ud, Pd, m, tol=tol, prec=rm.MIXED)[0])
-        with pytest.raises(rm.RmhmcError):
-            rm.set_stencil_shape(ctx, rm.SHAPE_KFORCE, rm.FP32, 18, 2, 128)
+                out[(mode, tol)] = host(rm.kinetic_force(ctx, Ud, Pd, m, tol=tol, prec=rm.MIXED)[0])
+        for bad in ((2, 128), (3, 256), (0, 256)):
+            with pytest.raises(rm.RmhmcError):
+                rm.set_stencil_shape(ctx, rm.SHAPE_KFORCE, rm.FP32, 18, *bad)
     for tol in (1e-6, 1e-9):
         assert rel_l2(out[(1, tol)], out[(0, tol)]) <= 1e-6, tol
+        assert rel_l2(out[(2, tol)], out[(0, tol)]) <= 1e-6, tol
     if np.prod(L) <= 4096:
         _, ref, _ = oracle.kinetic(L, U, P, m, tol=1e-13)
-        assert rel_l2(out[(1, 1e-9)], ref) <= 1e-5
+        for mode in (0, 1, 2):
+            assert rel_l2(out[(mode, 1e-9)], ref) <= 1e-5
