@@ -195,10 +195,10 @@ int rmhmc_tuning(const rmhmc_ctx* ctx, char* buf, int len);
 #define RMHMC_SHAPE_LAP 0
 #define RMHMC_SHAPE_CG  1
 #define RMHMC_SHAPE_KFORCE 2   /* the mixed kinetic force's basis contraction (prec RMHMC_FP32, linkfmt 18): nmu 0,
-                                  block 128: four lanes per link, the block's own basis rows read from global
-                                  memory once per chunk of 4; nmu 1, block 128: the same rows staged once in
-                                  shared memory (runs of up to 20 vectors); nmu 2, block 256 (the default): eight
-                                  lanes per link splitting the rows of the 8x8 accumulator, chunks of 8 */
+                                  block 128 (the default): four lanes per link, the block's own basis rows read
+                                  from global memory once per chunk of 4; nmu 1, block 128: the same rows staged
+                                  once in shared memory (runs of up to 20 vectors); nmu 2, block 256: eight lanes
+                                  per link splitting the rows of the 8x8 accumulator, chunks of 8 */
 #define RMHMC_SHAPE_LINKUPDATE 3   /* the float64 link update exp(i eps V) U (prec RMHMC_FP64, linkfmt 18, block
                                       128): nmu 1 (the default) in float-float arithmetic (two float32 numbers per
                                       value, ~2^-48 relative; rotations with Tr Q^2 / 2 >= 0.24 in float64), nmu 0

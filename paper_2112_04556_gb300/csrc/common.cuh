@@ -319,8 +319,9 @@ struct rmhmc_ctx {
     // autotuned stencil shapes per (precision bytes * 100 + link format): components per lane, block size
     std::map<int, std::pair<int, int>> tune;
     // kernel of the kinetic-force contraction (rmhmc_set_stencil_shape, RMHMC_SHAPE_KFORCE): 0 four lanes per link,
-    // own basis rows from global memory; 1 the same with the rows staged in shared memory; 2 eight lanes per link
-    int lg_mode = 2;
+    // own basis rows from global memory (the fastest at 32^4: 9.9 ms per kinetic evaluation against 11.2 and
+    // 11.5 ms); 1 the same with the rows staged in shared memory; 2 eight lanes per link
+    int lg_mode = 0;
     // float64 link update in float-float arithmetic (rmhmc_set_stencil_shape, RMHMC_SHAPE_LINKUPDATE)
     bool link_update_ff = true;
     std::string tune_report;

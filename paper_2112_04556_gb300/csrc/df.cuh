@@ -32,13 +32,12 @@ __device__ __forceinline__ dfl quick_two_sum(float a, float b) {
     const float s = __fadd_rn(a, b);
     return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
+// a + b with an error below 2^-47 (|a| + |b|): the low parts are added without their own TwoSum, which is
+// accurate relative to the operands (not to a cancelled result) -- enough here, where every value is an
+// entry or coefficient of order 1 and the link update needs absolute accuracy
 __device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-    dfl s = two_sum(a.hi, b.hi);
-    const dfl t = two_sum(a.lo, b.lo);
-    s.lo = __fadd_rn(s.lo, t.hi);
-    s = quick_two_sum(s.hi, s.lo);
-    s.lo = __fadd_rn(s.lo, t.lo);
-    return quick_two_sum(s.hi, s.lo);
+    const dfl s = two_sum(a.hi, b.hi);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ dfl df_neg(dfl a) { return df_make(-a.hi, -a.lo); }
 __device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
