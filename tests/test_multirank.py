@@ -69,7 +69,9 @@ def test_reference_arm_json_line(capsys):
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "traj/s"
     assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1
-    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 / d["value"]) < 1e-6 * d["ms_per_step"]
+    # each step is a bounded sample covering units_per_step of one trajectory: value = units / seconds
+    assert d["value"] > 0 and 0 < d["units_per_step"] < 1
+    assert abs(d["value"] - d["units_per_step"] / (d["ms_per_step"] * 1e-3)) < 1e-9 * d["value"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "traj/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
