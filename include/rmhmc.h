@@ -202,7 +202,13 @@ int rmhmc_tuning(const rmhmc_ctx* ctx, char* buf, int len);
 #define RMHMC_SHAPE_LINKUPDATE 3   /* the float64 link update exp(i eps V) U (prec RMHMC_FP64, linkfmt 18, block
                                       128): nmu 1 (the default) in float-float arithmetic (two float32 numbers per
                                       value, ~2^-48 relative; rotations with Tr Q^2 / 2 >= 0.24 in float64), nmu 0
-                                      in float64 throughout */
+                                      in float64 throughout.  Applies to rmhmc_link_update and the mixed-precision
+                                      trajectories; float64 trajectories and the flow stay in float64 */
+#define RMHMC_SHAPE_ADJOINT 4   /* the multi-field adjoint-form stencil (lap_apply of 6 or more float32 fields, the
+                                   batched Chebyshev recurrence; prec RMHMC_FP32, linkfmt 12 or 18): nmu = fields
+                                   per pass and parity, 2 or 3 (0: timed on first use, the default); block = the
+                                   z-extent of the slabs in which the grid sweeps t, 1 .. L2 (0: L2, i.e.
+                                   lexicographic order, the default) */
 int rmhmc_set_stencil_shape(rmhmc_ctx* ctx, int kernel, int prec, int linkfmt, int nmu, int block);
 
 /* ---------------------------------------------------------------------------------------------- */
@@ -336,7 +342,9 @@ int rmhmc_gauss_field(rmhmc_ctx* ctx, double* out, uint64_t seed, uint32_t strea
                       cudaStream_t stream);
 
 /* Uout = exp(i eps V) U per link (device canonical links; Uout may equal U); the exponential is the
- * Cayley-Hamilton form, followed by reunitarisation if reunit != 0. */
+ * Cayley-Hamilton form, followed by reunitarisation if reunit != 0.  Computed in float-float arithmetic
+ * (~2^-48 relative) unless RMHMC_SHAPE_LINKUPDATE pins float64, as in the mixed-precision trajectories; the
+ * float64 trajectories and the gradient flow always update links in float64. */
 int rmhmc_link_update(rmhmc_ctx* ctx, const double* U, const double* V, double eps, int reunit,
                       double* Uout, cudaStream_t stream);
 

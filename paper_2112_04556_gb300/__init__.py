@@ -200,7 +200,7 @@ def set_graphs(ctx, on=True):
     ctx.check(lib().rmhmc_set_graphs(ctx.h, int(bool(on))))
 
 
-SHAPE_LAP, SHAPE_CG, SHAPE_KFORCE, SHAPE_LINKUPDATE = 0, 1, 2, 3
+SHAPE_LAP, SHAPE_CG, SHAPE_KFORCE, SHAPE_LINKUPDATE, SHAPE_ADJOINT = 0, 1, 2, 3, 4
 
 
 def set_stencil_shape(ctx, kernel, prec, linkfmt, nmu, block):

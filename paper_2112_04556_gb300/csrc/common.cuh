@@ -167,12 +167,19 @@ __device__ __forceinline__ void load8(const float* p, float* x) {
     float4 a = __ldg(q), b = __ldg(q + 1);
     x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
 }
-// eight floats with one 256-bit read-only global load (sm_100 and later).  p must be 32-byte aligned and
-// the data must not change during the kernel: used on the context's own buffers only.
+// eight floats with one 256-bit read-only global load (sm_100 and later).  p must be 32-byte aligned (callers
+// check it, or pass the context's own buffers) and no thread may write the data during the kernel before
+// this read.
 __device__ __forceinline__ void load8_v8(const float* p, float* x) {
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
         : "l"(p));
+}
+// eight floats with one 256-bit global store; p 32-byte aligned
+__device__ __forceinline__ void store8_v8(float* p, const float* x) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(x[0]), "f"(x[1]), "f"(x[2]),
+                 "f"(x[3]), "f"(x[4]), "f"(x[5]), "f"(x[6]), "f"(x[7])
+                 : "memory");
 }
 __device__ __forceinline__ void store8(double* p, const double* x) {
     double2* q = reinterpret_cast<double2*>(p);
@@ -324,6 +331,11 @@ struct rmhmc_ctx {
     int lg_mode = 0;
     // float64 link update in float-float arithmetic (rmhmc_set_stencil_shape, RMHMC_SHAPE_LINKUPDATE)
     bool link_update_ff = true;
+    // z-extent of the multi-field adjoint kernel's slabs (rmhmc_set_stencil_shape, RMHMC_SHAPE_ADJOINT); 0 chosen
+    // from the lattice and the field count
+    int ad_slab = 0;
+    // incremented by every rmhmc_set_stencil_shape: part of the key of a captured trajectory graph
+    int shape_gen = 0;
     std::string tune_report;
     // counters: kernels launched; optional timing of the conjugate-gradient stencil launches
     long long launches = 0;

@@ -228,6 +228,7 @@ extern "C" int rmhmc_tuning(const rmhmc_ctx* ctx, char* buf, int len) {
 extern "C" int rmhmc_set_stencil_shape(rmhmc_ctx* ctx, int kernel, int prec, int linkfmt, int nmu, int block) {
     if (!ctx) return RMHMC_EINVAL;
     ctx->err.clear();
+    ctx->shape_gen++;
     if (kernel == RMHMC_SHAPE_LINKUPDATE) {
         if (prec != RMHMC_FP64 || linkfmt != 18 || (nmu != 0 && nmu != 1) || block != 128)
             return set_err(ctx, RMHMC_EINVAL, "link update: RMHMC_FP64, 18, nmu 0 or 1, block 128");
@@ -238,6 +239,20 @@ extern "C" int rmhmc_set_stencil_shape(rmhmc_ctx* ctx, int kernel, int prec, int
         if (prec != RMHMC_FP32 || linkfmt != 18 || nmu < 0 || nmu > 2 || block != (nmu == 2 ? 256 : 128))
             return set_err(ctx, RMHMC_EINVAL, "kinetic-force contraction: RMHMC_FP32, 18, nmu 0/1 with block 128 or 2 with 256");
         ctx->lg_mode = nmu;
+        return RMHMC_OK;
+    }
+    if (kernel == RMHMC_SHAPE_ADJOINT) {
+        if (prec != RMHMC_FP32 || (linkfmt != 12 && linkfmt != 18) || (nmu != 0 && nmu != 2 && nmu != 3) ||
+            block < 0 || block > ctx->g.L[2])
+            return set_err(ctx, RMHMC_EINVAL, "adjoint kernel: RMHMC_FP32, 12 or 18, nmu 0/2/3, block 0..L2");
+        const int key = 20000 + linkfmt;
+        if (nmu == 0) ctx->tune.erase(key);
+        else ctx->tune[key] = {nmu - 2, 0};
+        ctx->ad_slab = block;
+        char line[96];
+        snprintf(line, sizeof line, "%sadjoint LF%d pinned -> %d fields/pass, slab depth %d",
+                 ctx->tune_report.empty() ? "" : "; ", linkfmt, nmu, block);
+        ctx->tune_report += line;
         return RMHMC_OK;
     }
     if (kernel != RMHMC_SHAPE_LAP && kernel != RMHMC_SHAPE_CG) return set_err(ctx, RMHMC_EINVAL, "bad kernel");

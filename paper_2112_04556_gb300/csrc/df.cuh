@@ -19,7 +19,6 @@ __device__ __forceinline__ dfl df_from(double x) {
     return df_make(h, __double2float_rn(x - (double)h));
 }
 __device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
-
 // s + e = a + b exactly (TwoSum)
 __device__ __forceinline__ dfl two_sum(float a, float b) {
     const float s = __fadd_rn(a, b);
@@ -32,6 +31,37 @@ __device__ __forceinline__ dfl quick_two_sum(float a, float b) {
     const float s = __fadd_rn(a, b);
     return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
+// The same conversions from the IEEE-754 bit fields, with integer operations and no float64 arithmetic (float64
+// runs at a small fraction of the float32 rate on this part).  df_split: hi = x with its 29 low significand
+// bits cleared (24 significant bits: exactly a float), lo = those 29 bits as a float (rounded to 24 bits) times
+// 2^(e - 52), then renormalised so that |lo| <= ulp(hi) / 2.  |x| below 2^-126 gives 0 and |x| at or above
+// 2^128 gives +-inf (NaN too); lo is dropped for |x| < 2^-74 (an absolute error below 2^-97).
+__device__ __forceinline__ dfl df_split(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 1023 - 126) return df_make(__uint_as_float(sign), __uint_as_float(sign));
+    if (e > 1023 + 127) return df_make(__uint_as_float(sign | 0x7f800000u), 0.f);
+    const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    float lo = 0.f;
+    if (e >= 949) {   // 2^(e - 1075) is a normal float
+        lo = __int2float_rn((int)(b & 0x1fffffffull)) * __uint_as_float((unsigned)(e - 948) << 23);
+        if (sign) lo = -lo;
+    }
+    return quick_two_sum(hi, lo);
+}
+// a float as a double, from its bit fields (normal numbers, zero, inf and NaN; subnormals give 0)
+__device__ __forceinline__ double f_to_d_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned fe = (u >> 23) & 0xffu;
+    if (fe == 0) return __longlong_as_double((long long)sign);
+    const unsigned long long de = fe == 255 ? 0x7ffull : (unsigned long long)(fe - 127 + 1023);
+    return __longlong_as_double((long long)(sign | (de << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+// hi + lo as a double: one float64 addition, exact (the two parts span at most 49 bits)
+__device__ __forceinline__ double df_join(dfl a) { return f_to_d_bits(a.hi) + f_to_d_bits(a.lo); }
+
 // a + b with an error below 2^-47 (|a| + |b|): the low parts are added without their own TwoSum, which is
 // accurate relative to the operands (not to a cancelled result) -- enough here, where every value is an
 // entry or coefficient of order 1 and the link update needs absolute accuracy

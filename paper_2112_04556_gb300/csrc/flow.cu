@@ -40,14 +40,14 @@ extern "C" int wilson_flow(rmhmc_ctx* ctx, double* U, double eps, int nsteps, in
     const double g2 = 6.0;   // g0^2 F = 6 F(beta = 1)
     for (int n = 0; n < nsteps; n++) {
         RM_TRY(gauge_force_launch(ctx, 1.0, 0.0, gprec, Z0, stream));
-        RM_TRY(link_update_launch(ctx, U, Z0, 0.25 * g2 * eps, false, W, nullptr, nullptr, true, stream));
+        RM_TRY(link_update_launch(ctx, U, Z0, 0.25 * g2 * eps, false, W, nullptr, nullptr, true, false, stream));
         RM_TRY(gauge_force_launch(ctx, 1.0, 0.0, gprec, Z1, stream));
         RM_TRY(axpby64(ctx, 8.0 / 9.0, Z1, -17.0 / 36.0, Z0, Zc, fs, stream));
-        RM_TRY(link_update_launch(ctx, W, Zc, g2 * eps, false, W, nullptr, nullptr, true, stream));
+        RM_TRY(link_update_launch(ctx, W, Zc, g2 * eps, false, W, nullptr, nullptr, true, false, stream));
         RM_TRY(gauge_force_launch(ctx, 1.0, 0.0, gprec, Z2, stream));
         RM_TRY(axpby64(ctx, 0.75, Z2, -8.0 / 9.0, Z1, Zc, fs, stream));
         RM_TRY(axpby64(ctx, 1.0, Zc, 17.0 / 36.0, Z0, Zc, fs, stream));
-        RM_TRY(link_update_launch(ctx, W, Zc, g2 * eps, false, U, nullptr, nullptr, true, stream));
+        RM_TRY(link_update_launch(ctx, W, Zc, g2 * eps, false, U, nullptr, nullptr, true, false, stream));
         if (E) RM_TRY(energy(E + n + 1));
     }
     RM_CHECK(ctx, cudaStreamSynchronize(stream));

@@ -219,13 +219,18 @@ __global__ void __launch_bounds__(kBlock) k_link_update(const double* __restrict
 // reunitarisation, all to ~2^-48 relative, at a fraction of the float64 cost.  Links with c1 >= 0.24 (a
 // rotation by more than about half a radian) take the float64 path of k_link_update.
 // ------------------------------------------------------------------------------------------------
-__constant__ double kInvFactorial[26] = {
-    1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040, 1.0 / 40320, 1.0 / 362880,
-    1.0 / 3628800.0, 1.0 / 39916800.0, 1.0 / 479001600.0, 1.0 / 6227020800.0, 1.0 / 87178291200.0,
-    1.0 / 1307674368000.0, 1.0 / 20922789888000.0, 1.0 / 355687428096000.0, 1.0 / 6402373705728000.0,
-    1.0 / 121645100408832000.0, 1.0 / 2432902008176640000.0, 1.0 / 51090942171709440000.0,
-    1.0 / 1124000727777607680000.0, 1.0 / 25852016738884976640000.0, 1.0 / 620448401733239439360000.0,
-    1.0 / 15511210043330985984000000.0};
+// 1/n! as float pairs (hi = the nearest float, lo = the nearest float to the remainder)
+#define RM_DFC(x) {(float)(x), (float)((x) - (double)(float)(x))}
+__constant__ float2 kInvFactorialDF[26] = {
+    RM_DFC(1.0), RM_DFC(1.0), RM_DFC(1.0 / 2), RM_DFC(1.0 / 6),
+    RM_DFC(1.0 / 24), RM_DFC(1.0 / 120), RM_DFC(1.0 / 720), RM_DFC(1.0 / 5040),
+    RM_DFC(1.0 / 40320), RM_DFC(1.0 / 362880), RM_DFC(1.0 / 3628800.0), RM_DFC(1.0 / 39916800.0),
+    RM_DFC(1.0 / 479001600.0), RM_DFC(1.0 / 6227020800.0), RM_DFC(1.0 / 87178291200.0), RM_DFC(1.0 / 1307674368000.0),
+    RM_DFC(1.0 / 20922789888000.0), RM_DFC(1.0 / 355687428096000.0), RM_DFC(1.0 / 6402373705728000.0), RM_DFC(1.0 / 121645100408832000.0),
+    RM_DFC(1.0 / 2432902008176640000.0), RM_DFC(1.0 / 51090942171709440000.0), RM_DFC(1.0 / 1124000727777607680000.0), RM_DFC(1.0 / 25852016738884976640000.0),
+    RM_DFC(1.0 / 620448401733239439360000.0), RM_DFC(1.0 / 15511210043330985984000000.0),
+};
+#undef RM_DFC
 
 struct hermdf { dfl d[3]; cdfl o[3]; };   // d: diagonal, o: 01, 02, 12
 
@@ -236,18 +241,22 @@ __device__ __forceinline__ cdfl hdf_entry(const hermdf& h, int i, int j) {
     return i < j ? h.o[idx] : cdf_conj(h.o[idx]);
 }
 
-// R = exp(i Q) U in float-float, Q = eps V (V: 8 float64 coefficients), optionally reunitarised
-__device__ __forceinline__ void link_update_df(const double (&v)[8], double eps, const mat3<double>& U, bool reunit,
+// R = exp(i Q) U in float-float, Q = eps V (V: 8 coefficients and U already split into float pairs), optionally
+// reunitarised
+__device__ __forceinline__ void link_update_df(const dfl (&v)[8], dfl eps, const cdfl (&Ud)[3][3], bool reunit,
                                                cdfl (&R)[3][3]) {
     // Q = eps sum_a v_a T^a: diagonal (v3 + v8/sqrt3, -v3 + v8/sqrt3, -2 v8/sqrt3)/2, off-diagonal (v1 - i v2)/2, ...
-    const double r3 = 0.57735026918962576451;
+    constexpr double kR3 = 0.57735026918962576451;   // 1/sqrt(3), split at compile time
+    const dfl r3 = df_make((float)kR3, (float)(kR3 - (double)(float)kR3));
+    const dfl he = df_make(0.5f * eps.hi, 0.5f * eps.lo);
+    const dfl w8 = df_mul(v[7], r3);
     hermdf Q;
-    Q.d[0] = df_from(0.5 * eps * (v[2] + v[7] * r3));
-    Q.d[1] = df_from(0.5 * eps * (-v[2] + v[7] * r3));
-    Q.d[2] = df_from(-eps * v[7] * r3);
-    Q.o[0] = cdf_make(df_from(0.5 * eps * v[0]), df_from(-0.5 * eps * v[1]));
-    Q.o[1] = cdf_make(df_from(0.5 * eps * v[3]), df_from(-0.5 * eps * v[4]));
-    Q.o[2] = cdf_make(df_from(0.5 * eps * v[5]), df_from(-0.5 * eps * v[6]));
+    Q.d[0] = df_mul(he, df_add(v[2], w8));
+    Q.d[1] = df_mul(he, df_sub(w8, v[2]));
+    Q.d[2] = df_neg(df_mul(eps, w8));
+    Q.o[0] = cdf_make(df_mul(he, v[0]), df_neg(df_mul(he, v[1])));
+    Q.o[1] = cdf_make(df_mul(he, v[3]), df_neg(df_mul(he, v[4])));
+    Q.o[2] = cdf_make(df_mul(he, v[5]), df_neg(df_mul(he, v[6])));
     // Q^2 (Hermitian), c1 = Tr Q^2 / 2, c0 = det Q
     const dfl n01 = cdf_norm(Q.o[0]), n02 = cdf_norm(Q.o[1]), n12 = cdf_norm(Q.o[2]);
     hermdf Q2;
@@ -266,7 +275,8 @@ __device__ __forceinline__ void link_update_df(const double (&v)[8], double eps,
     dfl fr[3] = {df_zero(), df_zero(), df_zero()}, fi[3] = {df_zero(), df_zero(), df_zero()};
     dfl a = df_make(1.f, 0.f), b = df_zero(), c = df_zero();
     for (int n = 0; n < 26; n++) {
-        const dfl inv = df_from(kInvFactorial[n]);
+        const float2 fz = kInvFactorialDF[n];
+        const dfl inv = df_make(fz.x, fz.y);
         const dfl sa = df_mul(inv, a), sb = df_mul(inv, b), sc = df_mul(inv, c);
         const int ph = n & 3;   // i^n = 1, i, -1, -i
         if (ph == 0) { fr[0] = df_add(fr[0], sa); fr[1] = df_add(fr[1], sb); fr[2] = df_add(fr[2], sc); }
@@ -288,11 +298,6 @@ __device__ __forceinline__ void link_update_df(const double (&v)[8], double eps,
             if (i == j) e = cdf_add(e, f0);
             E[i][j] = e;
         }
-    cdfl Ud[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) Ud[i][j] = cdf_make(df_from(U.e[i][j].re), df_from(U.e[i][j].im));
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -331,61 +336,98 @@ __global__ void __launch_bounds__(kBlock) k_link_update_ff(const double* __restr
     const int lk = blockIdx.x * blockDim.x + threadIdx.x;
     const int s = lk >> 2, mu = lk & 3;
     double diff = 0.0;
+    float diff32 = 0.f;   // the float-float branch's max |W_new - W_old|, from the float pairs
     if (s < nsite) {
         const size_t l = (size_t)s * 4 + mu;
         double v[8];
         load8(V + l * 8, v);
-        mat3<double> U;
-        const double2* src = reinterpret_cast<const double2*>(Uin + l * 18);
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) { const double2 z = src[3 * i + j]; U.e[i][j] = cmk(z.x, z.y); }
-        // c1 = Tr Q^2 / 2 = eps^2 |v|^2 / 4 decides the branch
+        // inputs split into float pairs by integer operations: the float-float branch runs no float64
+        // arithmetic except one addition per output value
+        dfl vs[8];
         float vv = 0.f;
 #pragma unroll
-        for (int a = 0; a < 8; a++) vv = fmaf((float)v[a], (float)v[a], vv);
-        const float c1 = 0.25f * (float)(eps * eps) * vv;
-        mat3<double> Rd;
+        for (int a = 0; a < 8; a++) {
+            vs[a] = df_split(v[a]);
+            vv = fmaf(vs[a].hi, vs[a].hi, vv);
+        }
+        const dfl es = df_split(eps);
+        // c1 = Tr Q^2 / 2 = eps^2 |v|^2 / 4 decides the branch
+        const float c1 = 0.25f * es.hi * es.hi * vv;
+        const double2* src = reinterpret_cast<const double2*>(Uin + l * 18);
+        double2* dst = reinterpret_cast<double2*>(Uout + l * 18);
+        const double2* old = Wold ? reinterpret_cast<const double2*>(Wold + l * 18) : nullptr;
         if (c1 < 0.24f) {
-            cdfl R[3][3];
-            link_update_df(v, eps, U, reunit != 0, R);
+            cdfl Ud[3][3], R[3][3];
 #pragma unroll
             for (int i = 0; i < 3; i++)
 #pragma unroll
-                for (int j = 0; j < 3; j++) Rd.e[i][j] = cmk(df_to(R[i][j].re), df_to(R[i][j].im));
+                for (int j = 0; j < 3; j++) {
+                    const double2 z = src[3 * i + j];
+                    Ud[i][j] = cdf_make(df_split(z.x), df_split(z.y));
+                }
+            link_update_df(vs, es, Ud, reunit != 0, R);
+            float rf[3][3][2];   // nearest float32 of each entry
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    const cdfl r = R[i][j];
+                    if (old) {
+                        const double2 o = old[3 * i + j];
+                        const dfl ore = df_split(o.x), oim = df_split(o.y);
+                        const float dr = __fadd_rn(__fsub_rn(r.re.hi, ore.hi), __fsub_rn(r.re.lo, ore.lo));
+                        const float di = __fadd_rn(__fsub_rn(r.im.hi, oim.hi), __fsub_rn(r.im.lo, oim.lo));
+                        diff32 = fmaxf(diff32, fmaxf(fabsf(dr), fabsf(di)));
+                    }
+                    const double2 z = make_double2(df_join(r.re), df_join(r.im));
+                    dst[3 * i + j] = z;
+                    if (u64) u64[(size_t)(mu * 9 + 3 * i + j) * nsite + s] = z;
+                    rf[i][j][0] = __fadd_rn(r.re.hi, r.re.lo);
+                    rf[i][j][1] = __fadd_rn(r.im.hi, r.im.lo);
+                }
+            if (u32a) {
+                u32a[(size_t)(mu * 3 + 0) * nsite + s] = make_float4(rf[0][0][0], rf[0][0][1], rf[0][1][0], rf[0][1][1]);
+                u32a[(size_t)(mu * 3 + 1) * nsite + s] = make_float4(rf[0][2][0], rf[0][2][1], rf[1][0][0], rf[1][0][1]);
+                u32a[(size_t)(mu * 3 + 2) * nsite + s] = make_float4(rf[1][1][0], rf[1][1][1], rf[1][2][0], rf[1][2][1]);
+#pragma unroll
+                for (int j = 0; j < 3; j++) u32b[(size_t)(mu * 3 + j) * nsite + s] = make_float2(rf[2][j][0], rf[2][j][1]);
+            }
         } else {
+            mat3<double> U;
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) { const double2 z = src[3 * i + j]; U.e[i][j] = cmk(z.x, z.y); }
             double w[8];
 #pragma unroll
             for (int a = 0; a < 8; a++) w[a] = v[a] * eps;
             herm<double> Q = coef_to_herm2(w);
 #pragma unroll
             for (int k = 0; k < 3; k++) { Q.d[k] *= 0.5; Q.o[k] = cscale(Q.o[k], 0.5); }
-            Rd = m_mul(expi<double>(Q), U);
+            mat3<double> Rd = m_mul(expi<double>(Q), U);
             if (reunit) reunitarise(Rd);
-        }
-        double2* dst = reinterpret_cast<double2*>(Uout + l * 18);
-        const double2* old = Wold ? reinterpret_cast<const double2*>(Wold + l * 18) : nullptr;
 #pragma unroll
-        for (int i = 0; i < 3; i++)
+            for (int i = 0; i < 3; i++)
 #pragma unroll
-            for (int j = 0; j < 3; j++) {
-                const double2 z = make_double2(Rd.e[i][j].re, Rd.e[i][j].im);
-                if (old) {
-                    const double2 o = old[3 * i + j];
-                    diff = fmax(diff, fmax(fabs(z.x - o.x), fabs(z.y - o.y)));
+                for (int j = 0; j < 3; j++) {
+                    const double2 z = make_double2(Rd.e[i][j].re, Rd.e[i][j].im);
+                    if (old) {
+                        const double2 o = old[3 * i + j];
+                        diff = fmax(diff, fmax(fabs(z.x - o.x), fabs(z.y - o.y)));
+                    }
+                    dst[3 * i + j] = z;
+                    if (u64) u64[(size_t)(mu * 9 + 3 * i + j) * nsite + s] = z;
                 }
-                dst[3 * i + j] = z;
-                if (u64) u64[(size_t)(mu * 9 + 3 * i + j) * nsite + s] = z;
-            }
-        if (u32a) {
-            u32a[(size_t)(mu * 3 + 0) * nsite + s] = make_float4(Rd.e[0][0].re, Rd.e[0][0].im, Rd.e[0][1].re, Rd.e[0][1].im);
-            u32a[(size_t)(mu * 3 + 1) * nsite + s] = make_float4(Rd.e[0][2].re, Rd.e[0][2].im, Rd.e[1][0].re, Rd.e[1][0].im);
-            u32a[(size_t)(mu * 3 + 2) * nsite + s] = make_float4(Rd.e[1][1].re, Rd.e[1][1].im, Rd.e[1][2].re, Rd.e[1][2].im);
+            if (u32a) {
+                u32a[(size_t)(mu * 3 + 0) * nsite + s] = make_float4(Rd.e[0][0].re, Rd.e[0][0].im, Rd.e[0][1].re, Rd.e[0][1].im);
+                u32a[(size_t)(mu * 3 + 1) * nsite + s] = make_float4(Rd.e[0][2].re, Rd.e[0][2].im, Rd.e[1][0].re, Rd.e[1][0].im);
+                u32a[(size_t)(mu * 3 + 2) * nsite + s] = make_float4(Rd.e[1][1].re, Rd.e[1][1].im, Rd.e[1][2].re, Rd.e[1][2].im);
 #pragma unroll
-            for (int j = 0; j < 3; j++) u32b[(size_t)(mu * 3 + j) * nsite + s] = make_float2(Rd.e[2][j].re, Rd.e[2][j].im);
+                for (int j = 0; j < 3; j++) u32b[(size_t)(mu * 3 + j) * nsite + s] = make_float2(Rd.e[2][j].re, Rd.e[2][j].im);
+            }
         }
     }
+    diff = fmax(diff, (double)diff32);
     if (maxdiff) {
         __shared__ double sh[kBlock / 32];
 #pragma unroll
@@ -643,9 +685,9 @@ __global__ void k_gauss_field(double* __restrict__ out, int V, uint64_t seed, ui
 // host driver
 // ------------------------------------------------------------------------------------------------
 int link_update_launch(rmhmc_ctx* ctx, const double* Uin, const double* V, double eps, bool reunit, double* Uout,
-                       const double* Wold, double* dmax, bool internal, cudaStream_t st) {
+                       const double* Wold, double* dmax, bool internal, bool ff, cudaStream_t st) {
     const int grid = lane_blocks(ctx);   // 4 V threads
-    if (ctx->link_update_ff)
+    if (ff && ctx->link_update_ff)
         k_link_update_ff<<<grid, kBlock, 0, st>>>(Uin, V, eps, reunit ? 1 : 0, Uout, Wold, dmax,
                                                   internal ? ctx->u64 : nullptr, internal ? ctx->u32a : nullptr,
                                                   internal ? ctx->u32b : nullptr, ctx->g.V);
@@ -771,6 +813,7 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
     const size_t fs = field_elems(ctx), lb = sizeof(double) * (size_t)ctx->g.V * 72;
     const double eps = p->tau / p->nsteps;
     const int gprec = md_gauge_prec(p);
+    const bool ff = p->prec == RMHMC_MIXED;   // float-float link updates in mixed precision only
     int fp_p = 0, fp_u = 0, solves = 0;
     long long kiters = 0;
     double worst = 0.0;
@@ -806,9 +849,9 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
         const bool it32 = link_iterates_fp32(p);
         // symplectic: P_h = dexp^{-1}_{-X1} mu (X1 = eps/2 V0); the link loop then also iterates mu2 = dexp_{X2} P_h
         if (p->symplectic) RM_TRY(mom_dexp(ctx, p->prec, true, w.Q, 0.5 * eps, nullptr, nullptr, w.V0, nullptr, w.Ph, nullptr, st));
-        RM_TRY(link_update_launch(ctx, U, w.V0, 0.5 * eps, false, w.B, nullptr, nullptr, false, st));
+        RM_TRY(link_update_launch(ctx, U, w.V0, 0.5 * eps, false, w.B, nullptr, nullptr, false, ff, st));
         if (it32) RM_TRY(link_iter32_launch(ctx, U, w.V0, eps, w.W32, false, nullptr, st));
-        else RM_TRY(link_update_launch(ctx, U, w.V0, eps, false, w.W, nullptr, nullptr, true, st));
+        else RM_TRY(link_update_launch(ctx, U, w.V0, eps, false, w.W, nullptr, nullptr, true, ff, st));
         conv = false;
         extra = -1;
         for (int i = 0; i < p->fp_maxit; i++) {
@@ -819,7 +862,7 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
             RM_CHECK(ctx, cudaMemsetAsync(w.dmax, 0, sizeof(double), st));
             // W_{i+1} (float64: into U's buffer, U is no longer needed as B holds exp(i eps/2 V0) U)
             if (it32) RM_TRY(link_iter32_launch(ctx, w.B, w.V0, 0.5 * eps, w.W32, true, w.dmax, st));
-            else RM_TRY(link_update_launch(ctx, w.B, w.V0, 0.5 * eps, false, U, w.W, w.dmax, true, st));
+            else RM_TRY(link_update_launch(ctx, w.B, w.V0, 0.5 * eps, false, U, w.W, w.dmax, true, ff, st));
             if (p->symplectic) RM_TRY(mom_dexp(ctx, p->prec, false, w.Ph, 0.5 * eps, nullptr, nullptr, w.V0, w.Q, w.Q, w.dmax, st));
             double d = 0.0;
             RM_TRY(read_max(ctx, w.dmax, &d, st));
@@ -832,8 +875,8 @@ static int md_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params* p, c
         }
         if (!conv) return set_err(ctx, RMHMC_ENOCONV, "link fixed point: no convergence in %d iterations", p->fp_maxit);
         // the accepted links, reunitarised, with fresh internal copies
-        if (it32) RM_TRY(link_update_launch(ctx, w.B, w.V0, 0.5 * eps, true, U, nullptr, nullptr, true, st));
-        else RM_TRY(link_update_launch(ctx, w.W, w.V0, 0.0, true, U, nullptr, nullptr, true, st));
+        if (it32) RM_TRY(link_update_launch(ctx, w.B, w.V0, 0.5 * eps, true, U, nullptr, nullptr, true, ff, st));
+        else RM_TRY(link_update_launch(ctx, w.W, w.V0, 0.0, true, U, nullptr, nullptr, true, ff, st));
         // (3) explicit half step with F_K(W_i, P') kept from the last iteration
         RM_TRY(potential_force(ctx, p, gprec, lg, w.FG, st));
         if (p->symplectic) RM_TRY(mom_dexp(ctx, p->prec, true, w.Q, 0.5 * eps, w.FG, w.FK, w.V0, nullptr, P, nullptr, st));
@@ -894,10 +937,12 @@ static int md_graph_bufs(rmhmc_ctx* ctx, MDGraphBufs& b) {
     return RMHMC_OK;
 }
 
-static std::string md_key(const rmhmc_params* p, const MassTerm& m) {
+// a captured trajectory is reused while the parameters, the mass term and the pinned kernel shapes are the same
+static std::string md_key(const rmhmc_ctx* ctx, const rmhmc_params* p, const MassTerm& m) {
     char buf[512];
-    snprintf(buf, sizeof buf, "%d|%.17g|%.17g|%.17g|%d|%.17g|%.17g|%d|%d|%d|%d|%.17g|%d", p->prec, p->beta, p->c1, p->tau,
-             p->nsteps, p->tol_md, p->fp_tol, p->fp_maxit, p->fp_extra, md_gauge_prec(p), p->maxiter, m.c, m.npole());
+    snprintf(buf, sizeof buf, "%d|%.17g|%.17g|%.17g|%d|%.17g|%.17g|%d|%d|%d|%d|%.17g|%d|%d", p->prec, p->beta, p->c1,
+             p->tau, p->nsteps, p->tol_md, p->fp_tol, p->fp_maxit, p->fp_extra, md_gauge_prec(p), p->maxiter, m.c,
+             m.npole(), ctx->shape_gen);
     std::string k(buf);
     for (int j = 0; j < m.npole(); j++) {
         snprintf(buf, sizeof buf, "|%.17g,%.17g", m.alpha[j], m.sigma[j]);
@@ -911,6 +956,7 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
     cudaStream_t st = ctx->cap_st[0], aux = ctx->cap_st[1], aux2 = ctx->cap_st[2];
     const double eps = p->tau / p->nsteps;
     const int gprec = md_gauge_prec(p);
+    const bool ff = p->prec == RMHMC_MIXED;
     RM_CHECK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     int s = RMHMC_OK;
     do {
@@ -953,9 +999,9 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
             if (s != RMHMC_OK) break;
             // (2) link fixed point (float32 iterates and the accepted one in float64, or float64 iterates)
             const bool it32 = link_iterates_fp32(p);
-            if ((s = link_update_launch(ctx, gb.U, w.V0, 0.5 * eps, false, w.B, nullptr, nullptr, false, st)) != RMHMC_OK) break;
+            if ((s = link_update_launch(ctx, gb.U, w.V0, 0.5 * eps, false, w.B, nullptr, nullptr, false, ff, st)) != RMHMC_OK) break;
             if (it32) s = link_iter32_launch(ctx, gb.U, w.V0, eps, w.W32, false, nullptr, st);
-            else s = link_update_launch(ctx, gb.U, w.V0, eps, false, w.W, nullptr, nullptr, true, st);
+            else s = link_update_launch(ctx, gb.U, w.V0, eps, false, w.W, nullptr, nullptr, true, ff, st);
             if (s != RMHMC_OK) break;
             if (cudaMemsetAsync(w.dmax, 0, sizeof(double), st) != cudaSuccess ||
                 cudaMemsetAsync(gb.ints + 1, 0, sizeof(int), st) != cudaSuccess ||
@@ -971,7 +1017,7 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
             s = kinetic_enqueue(ctx, m, w.Q, p->tol_md, p->maxiter, w.FK, w.V0, gb.stats, gb.ints, aux, aux2);
             if (s == RMHMC_OK && it32) s = link_iter32_launch(ctx, w.B, w.V0, 0.5 * eps, w.W32, true, w.dmax, aux);
             if (s == RMHMC_OK && !it32) {
-                s = link_update_launch(ctx, w.B, w.V0, 0.5 * eps, false, gb.U, w.W, w.dmax, true, aux);
+                s = link_update_launch(ctx, w.B, w.V0, 0.5 * eps, false, gb.U, w.W, w.dmax, true, ff, aux);
                 if (s == RMHMC_OK && cudaMemcpyAsync(w.W, gb.U, lb, cudaMemcpyDeviceToDevice, aux) != cudaSuccess)
                     s = RMHMC_ECUDA;
             }
@@ -986,8 +1032,8 @@ static int md_graph_capture(rmhmc_ctx* ctx, const rmhmc_params* p, const MassTer
             }
             if (s != RMHMC_OK) break;
             // the accepted links in float64, reunitarised; (3) explicit half step, next initial guess
-            if (it32) s = link_update_launch(ctx, w.B, w.V0, 0.5 * eps, true, gb.U, nullptr, nullptr, true, st);
-            else s = link_update_launch(ctx, w.W, w.V0, 0.0, true, gb.U, nullptr, nullptr, true, st);
+            if (it32) s = link_update_launch(ctx, w.B, w.V0, 0.5 * eps, true, gb.U, nullptr, nullptr, true, ff, st);
+            else s = link_update_launch(ctx, w.W, w.V0, 0.0, true, gb.U, nullptr, nullptr, true, ff, st);
             if (s != RMHMC_OK) break;
             if ((s = potential()) != RMHMC_OK) break;
             if ((s = mom_update(ctx, w.Q, 0.5 * eps, w.FG, w.FK, nullptr, gb.P, nullptr, st)) != RMHMC_OK) break;
@@ -1027,7 +1073,7 @@ static int md_graph_run(rmhmc_ctx* ctx, double* U, double* P, const rmhmc_params
     }
     for (int i = 0; i < 3; i++)
         if (!ctx->cap_st[i]) RM_CHECK(ctx, cudaStreamCreateWithFlags(&ctx->cap_st[i], cudaStreamNonBlocking));
-    const std::string key = md_key(p, m) + (lg ? "|logdet" : "");
+    const std::string key = md_key(ctx, p, m) + (lg ? "|logdet" : "");
     if (!ctx->md_exec || ctx->md_key != key || ctx->md_gen != ctx->ws_gen) {
         if (ctx->md_exec) {
             cudaGraphExecDestroy(ctx->md_exec);
@@ -1130,7 +1176,7 @@ extern "C" int rmhmc_link_update(rmhmc_ctx* ctx, const double* U, const double* 
     if (!ctx) return RMHMC_EINVAL;
     ctx->err.clear();
     if (!U || !V || !Uout) return set_err(ctx, RMHMC_EINVAL, "rmhmc_link_update: null argument");
-    return link_update_launch(ctx, U, V, eps, reunit != 0, Uout, nullptr, nullptr, false, stream);
+    return link_update_launch(ctx, U, V, eps, reunit != 0, Uout, nullptr, nullptr, false, true, stream);
 }
 
 extern "C" int rmhmc_hamiltonian(rmhmc_ctx* ctx, const double* U, const double* P, const rmhmc_params* p, double* H,

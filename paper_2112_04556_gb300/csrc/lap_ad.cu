@@ -6,25 +6,32 @@
 // U X U^dag).  Float32 only; this is the stencil of the batched Chebyshev recurrence (all spectral fields
 // share one launch per step) and of multi-field lap_apply.
 //
-// Work of one block: a tile of kAdSites consecutive sites (lexicographic order).
+// Work of one block: a tile of kAdSites consecutive sites; tiles are taken in the order (z block, t, position
+// in the slab), slabs of bz whole xy-planes.  bz = L2 (the default) is the lexicographic order; a thinner slab
+// keeps the t-neighbours of a slab in L2 until they are read again (fewer DRAM bytes: 1.99 against 2.64 GB
+// read at 24^3 x 32 with 18 fields and bz = 12), at the cost of re-reading the z-neighbours at the block
+// faces; in time neither order won consistently, so it is a pinned option (RMHMC_SHAPE_ADJOINT).
 //   phase 1: thread (hop, site) loads one link -- U_h(x) for the forward hops h < 4, U_{h-4}(x - h) for the
 //            backward ones -- and stores Ad (forward) or Ad^T (backward) in shared memory, with the
-//            neighbour site of that hop;
-//   phase 2: thread (site, mu, field parity) accumulates the 8 rows of H(X_f)_mu for the fields f of its
-//            parity, CH at a time over the 8 hops, reading the adjoint rows from shared memory (padded so
-//            that a warp's 128-bit reads hit distinct bank quads) and the neighbour values from global
-//            memory (each thread its own fields: no load is issued twice), then writes Y_f(x)_mu and adds the
-//            per-field dots <Y,Y>, <Y,X> to per-warp float64 sums (deterministic order).
+//            neighbour site of that hop (both as the columns of an adjoint matrix, Ad(U^dag) = Ad(U)^T);
+//   phase 2: the 8 threads of a site own the 8 16-byte chunks of its 32 components (chunk j: component j/2,
+//            colours 4 (j%2) .. 4 (j%2) + 3), so that one 128-bit load instruction of a warp reads 4 whole
+//            128-byte lines (4 sites of one field).  Over the 8 hops a thread accumulates, CH fields at a time,
+//            the products of the four matching columns of each adjoint matrix (from shared memory, padded so
+//            that a warp's 128-bit reads hit distinct bank quads) with its chunk of the neighbour's value; the
+//            two column halves of a component are summed by one lane exchange, each lane keeping the rows of
+//            its own chunk.  Y_f(x) is written chunk by chunk, and the per-field dots <Y,Y>, <Y,X> go to
+//            per-warp float64 sums (deterministic order).
 #include "common.cuh"
 #include "ops.cuh"
 
 namespace rm {
 
 constexpr int kAdSites = 32;                 // sites per tile
-constexpr int kAdThreads = 256;              // 8 hops x 32 sites in phase 1; 32 sites x 4 mu x 2 parities in phase 2
+constexpr int kAdThreads = 256;              // 8 hops x 32 sites in phase 1; 32 sites x 8 chunks in phase 2
 constexpr int kAdHop = 64;                   // floats per (site, hop) record: 8 rows x 8
-constexpr int kAdSiteStride = 8 * kAdHop + 8;   // 520 floats: = 8 mod 32, so the 4 site records a warp reads in one
-                                                // 128-bit load fall on distinct bank quads
+constexpr int kAdSiteStride = 8 * kAdHop + 8;   // 520 floats: = 8 mod 32, so the 8 row halves (4 sites x 2) a
+                                                // warp reads in one 128-bit load fall on distinct bank quads
 constexpr size_t kAdSmemFloats = (size_t)kAdSites * kAdSiteStride;
 constexpr int kMaxDevices = 64;
 
@@ -34,11 +41,12 @@ inline size_t ad_smem_bytes(int nd) {
 }
 
 // CH: fields per pass of phase 2; MINB: resident blocks the register budget is compiled for
-template <int LF, bool HAS_W, bool DOTS, int CH, int MINB>
+template <int LF, bool HAS_W, bool DOTS, int CH, int MINB, bool V8>
 __global__ void __launch_bounds__(kAdThreads, MINB) k_lap_ad(Geom g, Links32 U, const float* __restrict__ X,
                                                         float* __restrict__ Y, const float* __restrict__ W, int nf,
-                                                        float a, float b, float c, size_t fs, double* partials,
-                                                        unsigned* counters, double* out, size_t slot_stride) {
+                                                        float a, float b, float c, size_t fs, int bz,
+                                                        double* partials, unsigned* counters, double* out,
+                                                        size_t slot_stride) {
     extern __shared__ __align__(16) float smem[];
     float* ad = smem;                                            // [kAdSites][kAdSiteStride]
     int* nbr = reinterpret_cast<int*>(smem + kAdSmemFloats);     // [kAdSites][8]
@@ -47,52 +55,61 @@ __global__ void __launch_bounds__(kAdThreads, MINB) k_lap_ad(Geom g, Links32 U, 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     if (DOTS)
         for (int i = t; i < (kAdThreads / 32) * nf * 2; i += kAdThreads) dsum[i] = 0.0;
-    const int ntile = (g.V + kAdSites - 1) / kAdSites;
     // phase-2 role of this thread: site, component, and the parity of its fields
     const int ps = t >> 3, pmu = (t >> 1) & 3, par = t & 1;
-    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    // work units in the order (z block, t, tile): a slab is bz whole xy-planes at one t, cut into tiles of
+    // kAdSites consecutive sites
+    const int P = g.stride[2], V3 = g.stride[3];
+    const int nts = (P * bz + kAdSites - 1) / kAdSites;
+    const int nunit = nts * g.L[3] * ((g.L[2] + bz - 1) / bz);
+    for (int u = blockIdx.x; u < nunit; u += gridDim.x) {
+        const int jt = u % nts, r = u / nts, tt = r % g.L[3], z0 = (r / g.L[3]) * bz;
+        const int first = jt * kAdSites;
+        const int nvalid = min(kAdSites, P * min(bz, g.L[2] - z0) - first);
+        if (nvalid <= 0) continue;   // a tile past the end of a thinner last z block (uniform over the block)
+        const int base = tt * V3 + z0 * P + first;
         // ---- phase 1: adjoint matrices of the 8 hops of every site in the tile
         {
             const int sl = t & (kAdSites - 1), hop = t >> 5;
-            const int s = tile * kAdSites + sl;
-            if (s < g.V) {
+            const int s = base + sl;
+            if (sl < nvalid) {
                 const int dir = hop & 3;
                 const int nb = hop < 4 ? step_site(g, s, dir, 1) : step_site(g, s, dir, -1);
                 const mat3<float> u = LinkLoad<float, LF>::load(U, hop < 4 ? s : nb, dir);
                 float* rec = ad + sl * kAdSiteStride + hop * kAdHop;
-                if (hop < 4) {
-                    // Ad row by row: column b lands in entry b of each row
-                    adjoint_columns(u, [&](int bcol, const float (&col)[8]) {
-#pragma unroll
-                        for (int r = 0; r < 8; r++) rec[r * 8 + bcol] = col[r];
-                    });
-                } else {
-                    // Ad^T: column b of Ad is row b of the record
-                    adjoint_columns(u, [&](int bcol, const float (&col)[8]) {
-                        float4* d = reinterpret_cast<float4*>(rec + bcol * 8);
-                        d[0] = make_float4(col[0], col[1], col[2], col[3]);
-                        d[1] = make_float4(col[4], col[5], col[6], col[7]);
-                    });
-                }
+                // record row b = column b of Ad(V): V = U^dag for a forward hop, since Ad(U^dag) = Ad(U)^T gives
+                // the rows of Ad(U); V = U for a backward hop, whose record is Ad(U)^T.  Whole rows are stored
+                // as two 128-bit words.
+                adjoint_columns(hop < 4 ? m_dag(u) : u, [&](int bcol, const float (&col)[8]) {
+                    float4* d = reinterpret_cast<float4*>(rec + bcol * 8);
+                    d[0] = make_float4(col[0], col[1], col[2], col[3]);
+                    d[1] = make_float4(col[4], col[5], col[6], col[7]);
+                });
                 nbr[sl * 8 + hop] = nb;
             }
         }
         __syncthreads();
         // ---- phase 2
-        const int s = tile * kAdSites + ps;
-        const bool active = s < g.V;
+        const int s = base + ps;
+        const bool active = ps < nvalid;
         const float* rec0 = ad + ps * kAdSiteStride;
         const int* nb = nbr + ps * 8;
         const float* Xm = X + pmu * 8;
         // fields of this thread: par, par + 2, par + 4, ...; pass p covers the CH fields par + 2 (p CH + q)
         const int mine = (nf - par + 1) / 2;
+        // 32 bytes of one component: one 256-bit load when the fields are 32-byte aligned (a warp's load then
+        // covers 8 whole 128-byte lines: 4 sites x 2 fields), else two 128-bit loads
+        auto ld8 = [&](const float* ptr, float (&x)[8]) {
+            if (V8) load8_v8(ptr, x);
+            else load8(ptr, x);
+        };
         // the (pass, hop) iterations are software-pipelined: the neighbour values of the next iteration are
         // loaded before the arithmetic of the current one
         auto load_x = [&](int q0, int hop, float (&x)[CH][8]) {
             const size_t n = (size_t)nb[hop] * 32;
 #pragma unroll
             for (int q = 0; q < CH; q++) {
-                if (active && q0 + q < mine) load8(Xm + (size_t)(par + 2 * (q0 + q)) * fs + n, x[q]);
+                if (active && q0 + q < mine) ld8(Xm + (size_t)(par + 2 * (q0 + q)) * fs + n, x[q]);
                 else
 #pragma unroll
                     for (int k = 0; k < 8; k++) x[q][k] = 0.f;
@@ -142,16 +159,17 @@ __global__ void __launch_bounds__(kAdThreads, MINB) k_lap_ad(Geom g, Links32 U, 
                 if (active && fi < mine) {
                     const size_t off = (size_t)f * fs + (size_t)s * 32 + pmu * 8;
                     float xo[8], y[8];
-                    load8(X + off, xo);
+                    ld8(X + off, xo);
 #pragma unroll
                     for (int r = 0; r < 8; r++) y[r] = fmaf(b, acc[q][r], a * xo[r]);
                     if (HAS_W) {
                         float w[8];
-                        load8(W + off, w);
+                        ld8(W + off, w);
 #pragma unroll
                         for (int r = 0; r < 8; r++) y[r] = fmaf(c, w[r], y[r]);
                     }
-                    store8(Y + off, y);
+                    if (V8) store8_v8(Y + off, y);
+                    else store8(Y + off, y);
                     if (DOTS) {
 #pragma unroll
                         for (int r = 0; r < 8; r++) { yy = fmaf(y[r], y[r], yy); yx = fmaf(y[r], xo[r], yx); }
@@ -171,7 +189,7 @@ __global__ void __launch_bounds__(kAdThreads, MINB) k_lap_ad(Geom g, Links32 U, 
                 }
             }
         }
-        __syncthreads();   // the next tile overwrites the adjoint records
+        __syncthreads();   // the next unit overwrites the adjoint records
     }
     if (DOTS) {
         // per field: the warps' sums in warp order, then the deterministic grid sum
@@ -190,13 +208,13 @@ __global__ void __launch_bounds__(kAdThreads, MINB) k_lap_ad(Geom g, Links32 U, 
 
 // launch shapes (fields per pass, blocks per SM), chosen per context by timing on first use
 struct AdShape { int ch, minb; };
-constexpr AdShape kAdShapes[3] = {{2, 3}, {3, 2}, {4, 2}};
+constexpr AdShape kAdShapes[2] = {{2, 3}, {3, 2}};
 
-template <int LF, bool HAS_W, bool DOTS, int CH, int MINB>
+template <int LF, bool HAS_W, bool DOTS, int CH, int MINB, bool V8>
 static int launch_ad_t(rmhmc_ctx* ctx, const float* X, float* Y, int nf, double a, double b, const float* W, double c,
                        int slot, cudaStream_t st) {
     if (DOTS && nf > kRedSlots) return set_err(ctx, RMHMC_EINVAL, "too many reduced fields");
-    auto kern = k_lap_ad<LF, HAS_W, DOTS, CH, MINB>;
+    auto kern = k_lap_ad<LF, HAS_W, DOTS, CH, MINB, V8>;
     const size_t smem = ad_smem_bytes(DOTS ? nf : 0);
     // the dynamic shared-memory limit of this instantiation, raised once per device to the largest size any
     // launch can ask for (kRedSlots reduced fields)
@@ -208,36 +226,46 @@ static int launch_ad_t(rmhmc_ctx* ctx, const float* X, float* Y, int nf, double 
     }
     int per_sm = 0;
     RM_CHECK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdThreads, smem));
-    const int ntile = (ctx->g.V + kAdSites - 1) / kAdSites;
-    const int grid = std::max(1, std::min(ntile, (int)ctx->num_sms * std::max(per_sm, 1)));
+    const int bz = ctx->ad_slab > 0 ? ctx->ad_slab : ctx->g.L[2];
+    const int P = ctx->g.stride[2];
+    const int nunit = (P * bz + kAdSites - 1) / kAdSites * ctx->g.L[3] * ((ctx->g.L[2] + bz - 1) / bz);
+    const int grid = std::max(1, std::min(nunit, (int)ctx->num_sms * std::max(per_sm, 1)));
     const size_t ss = (size_t)ctx->max_blocks * 2;
     double* part = DOTS ? red_slot_partials(ctx, slot) : nullptr;
     unsigned* cnt = DOTS ? red_slot_counter(ctx, slot) : nullptr;
     double* out = DOTS ? red_slot_out(ctx, slot) : nullptr;
     kern<<<grid, kAdThreads, smem, st>>>(ctx->g, links32(ctx), X, Y, W, nf, (float)a, (float)b, (float)c, field_elems(ctx),
-                                         part, cnt, out, ss);
+                                         bz, part, cnt, out, ss);
     ++ctx->launches;
     RM_LAUNCH_CHECK(ctx);
     return RMHMC_OK;
 }
 
+template <int LF, int CH, int MINB, bool V8>
+static int launch_ad_w(rmhmc_ctx* ctx, const float* X, float* Y, int nf, double a, double b, const float* W, double c,
+                       int slot, cudaStream_t st) {
+    if (W) {
+        if (slot >= 0) return launch_ad_t<LF, true, true, CH, MINB, V8>(ctx, X, Y, nf, a, b, W, c, slot, st);
+        return launch_ad_t<LF, true, false, CH, MINB, V8>(ctx, X, Y, nf, a, b, W, c, slot, st);
+    }
+    if (slot >= 0) return launch_ad_t<LF, false, true, CH, MINB, V8>(ctx, X, Y, nf, a, b, W, c, slot, st);
+    return launch_ad_t<LF, false, false, CH, MINB, V8>(ctx, X, Y, nf, a, b, W, c, slot, st);
+}
+
+// 256-bit accesses when every field array is 32-byte aligned (the context's own buffers always are)
 template <int LF, int CH, int MINB>
 static int launch_ad_shape(rmhmc_ctx* ctx, const float* X, float* Y, int nf, double a, double b, const float* W,
                            double c, int slot, cudaStream_t st) {
-    if (W) {
-        if (slot >= 0) return launch_ad_t<LF, true, true, CH, MINB>(ctx, X, Y, nf, a, b, W, c, slot, st);
-        return launch_ad_t<LF, true, false, CH, MINB>(ctx, X, Y, nf, a, b, W, c, slot, st);
-    }
-    if (slot >= 0) return launch_ad_t<LF, false, true, CH, MINB>(ctx, X, Y, nf, a, b, W, c, slot, st);
-    return launch_ad_t<LF, false, false, CH, MINB>(ctx, X, Y, nf, a, b, W, c, slot, st);
+    const bool v8 = (uintptr_t)X % 32 == 0 && (uintptr_t)Y % 32 == 0 && (uintptr_t)W % 32 == 0;
+    if (v8) return launch_ad_w<LF, CH, MINB, true>(ctx, X, Y, nf, a, b, W, c, slot, st);
+    return launch_ad_w<LF, CH, MINB, false>(ctx, X, Y, nf, a, b, W, c, slot, st);
 }
 
 template <int LF>
 static int launch_ad_idx(rmhmc_ctx* ctx, int k, const float* X, float* Y, int nf, double a, double b, const float* W,
                          double c, int slot, cudaStream_t st) {
     if (k == 0) return launch_ad_shape<LF, 2, 3>(ctx, X, Y, nf, a, b, W, c, slot, st);
-    if (k == 1) return launch_ad_shape<LF, 3, 2>(ctx, X, Y, nf, a, b, W, c, slot, st);
-    return launch_ad_shape<LF, 4, 2>(ctx, X, Y, nf, a, b, W, c, slot, st);
+    return launch_ad_shape<LF, 3, 2>(ctx, X, Y, nf, a, b, W, c, slot, st);
 }
 
 // the shape for this link format: on first use every shape is timed (one warm-up and three timed plain
@@ -257,7 +285,7 @@ static int ad_shape(rmhmc_ctx* ctx, const float* X, float* Y, int nf, cudaStream
     int bk = 0;
     char line[96];
     std::string rep;
-    for (int k = 0; k < 3; k++) {
+    for (int k = 0; k < 2; k++) {
         RM_TRY(launch_ad_idx<LF>(ctx, k, X, Y, nf, 0.5, -0.0625, nullptr, 0.0, -1, st));
         RM_CHECK(ctx, cudaEventRecord(e0, st));
         for (int r = 0; r < 3; r++) RM_TRY(launch_ad_idx<LF>(ctx, k, X, Y, nf, 0.5, -0.0625, nullptr, 0.0, -1, st));

@@ -30,8 +30,10 @@ int link_grad_launch(rmhmc_ctx* ctx, int prec, const void* X, const void* Z, int
                      cudaStream_t st);
 // Uout = exp(i eps V) Uin per link (float64, canonical [V][4][3][3]; in place allowed), optionally reunitarised;
 // with Wold, max |Uout - Wold| into *dmax; internal refreshes the context's link copies from Uout
+// ff: the float-float kernel may be used (when it is enabled, ctx->link_update_ff); the float64 trajectories
+// and the gradient flow pass false and stay in float64 throughout
 int link_update_launch(rmhmc_ctx* ctx, const double* Uin, const double* V, double eps, bool reunit, double* Uout,
-                       const double* Wold, double* dmax, bool internal, cudaStream_t st);
+                       const double* Wold, double* dmax, bool internal, bool ff, cudaStream_t st);
 // kinetic force G = sum_j alpha_j d<Z_j, A X_j>/dw straight from the float32 Krylov basis R (n vectors), with
 // X_j, Z_j given as rows of basis coefficients (rows j and ns + j, row stride ldr, device float64); n is
 // read on the device from flags[1] when flags is not null.  G float64 [V][4][8].

@@ -34,15 +34,20 @@ def test_link_update_matches_oracle(eps):
         assert np.abs(out2 - ref).max() <= 1e-13
 
 
-@pytest.mark.parametrize("eps", [1e-3, 0.05, 0.2, 0.7])
-def test_link_update_float_float_and_float64(eps):
+@pytest.mark.parametrize("eps,unit", [(1e-3, False), (0.05, False), (0.2, False), (0.7, False), (0.05, True)])
+def test_link_update_float_float_and_float64(eps, unit):
     """The float-float link update (the default) and the float64 one both match the oracle to 1e-13 and each
     other to 1e-14, with and without reunitarisation; at eps = 0.7 most links rotate far enough to take the
-    float64 branch inside the float-float kernel."""
+    float64 branch inside the float-float kernel.  Unit links (exact zeros and ones, whose float pairs come
+    from the zero-exponent and exact-power cases of the bit-field split) and momenta with exact zeros and a
+    tiny coefficient are included."""
     import paper_2112_04556_gb300 as rm
     L = (6, 4, 4, 5)
-    U = inputs.random_links(L, eps=0.5, seed=52)
+    U = inputs.unit_links(L) if unit else inputs.random_links(L, eps=0.5, seed=52)
     V = inputs.gaussian_fields(L, 1, seed=53)[0]
+    if unit:
+        V[::3, :, 2] = 0.0
+        V[1::7, 1, 5] = 3e-30
     ref = oracle.link_update(L, U, V, eps)
     out = {}
     with rm.Context(L) as ctx:
@@ -56,6 +61,28 @@ def test_link_update_float_float_and_float64(eps):
         assert np.abs(o - ref).max() <= 1e-13, key
     for reunit in (False, True):
         assert np.abs(out[(1, reunit)] - out[(0, reunit)]).max() <= 1e-14
+
+
+def test_float64_trajectory_keeps_float64_link_update():
+    """The float-float link update serves the mixed-precision trajectories only: a float64 trajectory gives the
+    same bits whether it is enabled (the default) or float64 is pinned; a mixed one stays within the fixed-point
+    tolerance of its float64-update twin."""
+    import paper_2112_04556_gb300 as rm
+    L = (4, 4, 4, 4)
+    U = inputs.random_links(L, eps=0.3, seed=61)
+    P = inputs.gaussian_fields(L, 1, seed=62)[0]
+    m = fit.mass_term(6, 0.9)
+    res = {}
+    for prec, kw in ((rm.FP64, {}), (rm.MIXED, dict(tol_md=1e-7, fp_tol=1e-6, fp_extra=2))):
+        for mode in (1, 0):
+            with rm.Context(L) as ctx:
+                rm.set_stencil_shape(ctx, rm.SHAPE_LINKUPDATE, rm.FP64, 18, mode, 128)
+                Ud, Pd = dev(U), dev(P)
+                rm.md(ctx, Ud, Pd, _params(rm, m, nsteps=3, prec=prec, **kw))
+                res[(prec, mode)] = (host(Ud), host(Pd))
+    for i in range(2):
+        assert np.array_equal(res[(rm.FP64, 1)][i], res[(rm.FP64, 0)][i])
+        assert np.abs(res[(rm.MIXED, 1)][i] - res[(rm.MIXED, 0)][i]).max() <= 1e-5
 
 
 def _params(rm, mass, **kw):

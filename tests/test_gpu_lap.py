@@ -174,7 +174,43 @@ def test_lap_link_centric_full_size_sampled():
 def test_set_stencil_shape_rejects():
     import paper_2112_04556_gb300 as rm
     with rm.Context((4, 4, 4, 4)) as ctx:
-        for args in [(2, rm.FP32, 18, 1, 128), (0, rm.FP64, 18, 8, 256), (0, rm.FP32, 18, 8, 128),
-                     (1, rm.FP32, 12, 2, 256), (0, rm.FP32, 18, 3, 256), (0, rm.FP32, 18, 2, 100)]:
+        for args in [(7, rm.FP32, 18, 1, 128), (0, rm.FP64, 18, 8, 256), (0, rm.FP32, 18, 8, 128),
+                     (1, rm.FP32, 12, 2, 256), (0, rm.FP32, 18, 3, 256), (0, rm.FP32, 18, 2, 100),
+                     (2, rm.FP32, 18, 1, 256), (3, rm.FP32, 18, 2, 128),
+                     (4, rm.FP64, 18, 2, 0), (4, rm.FP32, 18, 4, 0), (4, rm.FP32, 18, 1, 0), (4, rm.FP32, 18, 2, 5),
+                     (4, rm.FP32, 18, 2, -1), (4, rm.FP32, 16, 2, 0)]:
             with pytest.raises(rm.RmhmcError):
                 rm.set_stencil_shape(ctx, *args)
+        for args in [(4, rm.FP32, 18, 3, 2), (4, rm.FP32, 12, 0, 0), (4, rm.FP32, 18, 2, 4)]:
+            rm.set_stencil_shape(ctx, *args)
+
+
+@pytest.mark.parametrize("L", [(6, 5, 7, 9), (4, 8, 6, 5), (3, 2, 2, 4)])
+def test_lap_adjoint_every_shape_and_slab(L):
+    """The multi-field adjoint kernel with every fields-per-pass choice and slab depths that leave a thinner
+    last z block (7 = 3 + 3 + 1, 6 = 4 + 2), a slab that is not a whole number of 32-site tiles (5 x 6 x 2 =
+    60 sites) and one z block holding the whole lattice; 7 fields (the last pass ragged).  The fields are
+    also taken at an offset of 16 bytes, which the kernel reads with 128-bit instead of 256-bit accesses."""
+    import paper_2112_04556_gb300 as rm
+    torch = torch_cuda()
+    U = inputs.random_links(L, eps=0.7, seed=21)
+    X = inputs.gaussian_fields(L, 7, seed=22)
+    ref = oracle.lap(L, U, X)
+    X32 = dev(X, torch.float32)
+    # the same fields 16 bytes into a larger buffer
+    n = X32.numel()
+    buf = torch.zeros(2 * n + 8, dtype=torch.float32, device=X32.device)
+    Xo = buf[4:4 + n].view(X32.shape)
+    Xo.copy_(X32)
+    Yo = buf[n + 8:2 * n + 8].view(X32.shape)
+    assert Xo.data_ptr() % 32 == 16 and Yo.data_ptr() % 32 == 0
+    for ch, bz in [(2, 1), (3, 2), (2, 3), (3, 4), (2, L[2]), (3, 0)]:
+        bz = min(bz, L[2])
+        with rm.Context(L) as ctx:
+            Ud = dev(U)
+            for lf in (18, 12):
+                rm.set_stencil_shape(ctx, rm.SHAPE_ADJOINT, rm.FP32, lf, ch, bz)
+                Y = host(rm.lap_apply(ctx, Ud, X32, prec=rm.FP32, linkfmt=lf)).astype(np.float64)
+                assert rel_l2(Y, ref) <= 1e-5, (ch, bz, lf, rel_l2(Y, ref))
+                rm.lap_apply(ctx, None, Xo, Yo, prec=rm.FP32, linkfmt=lf)
+                assert rel_l2(host(Yo).astype(np.float64), ref) <= 1e-5, (ch, bz, lf, "offset")
