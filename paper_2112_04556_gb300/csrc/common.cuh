@@ -175,12 +175,6 @@ __device__ __forceinline__ void load8_v8(const float* p, float* x) {
         : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
         : "l"(p));
 }
-// eight floats with one 256-bit global store; p 32-byte aligned
-__device__ __forceinline__ void store8_v8(float* p, const float* x) {
-    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(x[0]), "f"(x[1]), "f"(x[2]),
-                 "f"(x[3]), "f"(x[4]), "f"(x[5]), "f"(x[6]), "f"(x[7])
-                 : "memory");
-}
 __device__ __forceinline__ void store8(double* p, const double* x) {
     double2* q = reinterpret_cast<double2*>(p);
 #pragma unroll

@@ -32,23 +32,29 @@ __device__ __forceinline__ dfl quick_two_sum(float a, float b) {
     return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
 // The same conversions from the IEEE-754 bit fields, with integer operations and no float64 arithmetic (float64
-// runs at a small fraction of the float32 rate on this part).  df_split: hi = x with its 29 low significand
-// bits cleared (24 significant bits: exactly a float), lo = those 29 bits as a float (rounded to 24 bits) times
-// 2^(e - 52), then renormalised so that |lo| <= ulp(hi) / 2.  |x| below 2^-126 gives 0 and |x| at or above
-// 2^128 gives +-inf (NaN too); lo is dropped for |x| < 2^-74 (an absolute error below 2^-97).
+// runs at a small fraction of the float32 rate on this part).  df_split: hi = x rounded to 24 significant bits
+// (its 29 low significand bits dropped, rounding half away from zero, a carry moving into the exponent), lo =
+// the signed remainder (at most 2^28 units of x's last place) as a float times 2^(e - 52); |lo| <= ulp(hi) / 2
+// and hi + lo = x to 2^-49 |x|, as for the float64 rounding of df_from.  |x| below 2^-126 gives 0 and |x|
+// near or above 2^128 gives +-inf (NaN too); lo is dropped for |x| < 2^-74 (an absolute error below 2^-98).
 __device__ __forceinline__ dfl df_split(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
     const int e = (int)((b >> 52) & 0x7ff);
     if (e < 1023 - 126) return df_make(__uint_as_float(sign), __uint_as_float(sign));
-    if (e > 1023 + 127) return df_make(__uint_as_float(sign | 0x7f800000u), 0.f);
-    const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    const unsigned long long m = b & 0x1fffffffull;
+    const bool up = m >= (1ull << 28);
+    const unsigned long long bh = (b & ~0x1fffffffull) + (up ? (1ull << 29) : 0ull);
+    const int eh = (int)((bh >> 52) & 0x7ff);
+    if (eh > 1023 + 127) return df_make(__uint_as_float(sign | 0x7f800000u), 0.f);
+    const float hi = __uint_as_float(sign | ((unsigned)(eh - 1023 + 127) << 23) | (unsigned)((bh >> 29) & 0x7fffffu));
     float lo = 0.f;
     if (e >= 949) {   // 2^(e - 1075) is a normal float
-        lo = __int2float_rn((int)(b & 0x1fffffffull)) * __uint_as_float((unsigned)(e - 948) << 23);
+        const int r = up ? (int)m - (1 << 29) : (int)m;
+        lo = __int2float_rn(r) * __uint_as_float((unsigned)(e - 948) << 23);
         if (sign) lo = -lo;
     }
-    return quick_two_sum(hi, lo);
+    return df_make(hi, lo);
 }
 // a float as a double, from its bit fields (normal numbers, zero, inf and NaN; subnormals give 0)
 __device__ __forceinline__ double f_to_d_bits(float f) {

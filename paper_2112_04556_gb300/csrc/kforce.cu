@@ -239,8 +239,8 @@ __global__ void __launch_bounds__(kLgSites * 4, 4) k_link_grad_krylov(Geom g, ty
 #pragma unroll
                 for (int b = 0; b < 8; b++) col[b] = C[b][d];
                 herm<T> E = h_zero<T>();
-                acc_uxud(E, u, coef_to_herm2(col));   // 2 sum_c (R C)_cd T^c
-                herm2_to_coef(E, rc);                  // (R C)_cd
+                acc_uxud_tl(E, u, coef_to_herm2(col));   // 2 sum_c (R C)_cd T^c
+                herm2_to_coef_tl(E, rc);                  // (R C)_cd
                 f_contract(d, rc, Gk);
             }
             double* out = G + (size_t)y * 32 + q * 8;
@@ -359,8 +359,8 @@ __global__ void __launch_bounds__(kLgSites * 4, 2) k_link_grad_staged(Geom g, Li
 #pragma unroll
                 for (int b = 0; b < 8; b++) col[b] = C[b][d];
                 herm<float> E = h_zero<float>();
-                acc_uxud(E, u, coef_to_herm2(col));   // 2 sum_c (R C)_cd T^c
-                herm2_to_coef(E, rc);                  // (R C)_cd
+                acc_uxud_tl(E, u, coef_to_herm2(col));   // 2 sum_c (R C)_cd T^c
+                herm2_to_coef_tl(E, rc);                  // (R C)_cd
                 f_contract(d, rc, Gk);
             }
             double* out = G + (size_t)y * 32 + q * 8;

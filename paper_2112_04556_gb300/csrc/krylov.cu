@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kBlockMax, (stencil_min_blocks<T, NMU>())) k_c
         for (int m = 0; m < NC; m++) {
             const int mu = mu0 + m;
             T h[8], x[8], y[8];
-            herm2_to_coef(acc[m], h);
+            herm2_to_coef_tl(acc[m], h);
             if constexpr (sizeof(T) == 4 && NMU == 1) load8_v8(r + (size_t)s * 32 + mu * 8, x);
             else load8(r + (size_t)s * 32 + mu * 8, x);
             T* qs = q + (size_t)s * 32 + mu * 8;
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kBlock) k_resid64(Geom g, Links64 U, const dou
         herm<double> acc;
         hop_sum1<double, LF>(g, U, s, mu, SrcField<double>{xf}, acc);
         double h[8], xx[8], bb[8], y[8];
-        herm2_to_coef(acc, h);
+        herm2_to_coef_tl(acc, h);
         load8(xf + (size_t)s * 32 + mu * 8, xx);
         load8(b + (size_t)s * 32 + mu * 8, bb);
 #pragma unroll

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kBlockMax, (stencil_min_blocks<T, NMU>())) k_l
         for (int m = 0; m < NC; m++) {
             const int mu = mu0 + m;
             T h[8], x[8], y[8];
-            herm2_to_coef(acc[m], h);
+            herm2_to_coef_tl(acc[m], h);
             load8(Xf + (size_t)s * 32 + mu * 8, x);
 #pragma unroll
             for (int k = 0; k < 8; k++) y[k] = fma(b, h[k], a * x[k]);

@@ -41,7 +41,7 @@ inline size_t ad_smem_bytes(int nd) {
 }
 
 // CH: fields per pass of phase 2; MINB: resident blocks the register budget is compiled for
-template <int LF, bool HAS_W, bool DOTS, int CH, int MINB, bool V8>
+template <int LF, bool HAS_W, bool DOTS, int CH, int MINB>
 __global__ void __launch_bounds__(kAdThreads, MINB) k_lap_ad(Geom g, Links32 U, const float* __restrict__ X,
                                                         float* __restrict__ Y, const float* __restrict__ W, int nf,
                                                         float a, float b, float c, size_t fs, int bz,
@@ -97,19 +97,13 @@ __global__ void __launch_bounds__(kAdThreads, MINB) k_lap_ad(Geom g, Links32 U, 
         const float* Xm = X + pmu * 8;
         // fields of this thread: par, par + 2, par + 4, ...; pass p covers the CH fields par + 2 (p CH + q)
         const int mine = (nf - par + 1) / 2;
-        // 32 bytes of one component: one 256-bit load when the fields are 32-byte aligned (a warp's load then
-        // covers 8 whole 128-byte lines: 4 sites x 2 fields), else two 128-bit loads
-        auto ld8 = [&](const float* ptr, float (&x)[8]) {
-            if (V8) load8_v8(ptr, x);
-            else load8(ptr, x);
-        };
         // the (pass, hop) iterations are software-pipelined: the neighbour values of the next iteration are
         // loaded before the arithmetic of the current one
         auto load_x = [&](int q0, int hop, float (&x)[CH][8]) {
             const size_t n = (size_t)nb[hop] * 32;
 #pragma unroll
             for (int q = 0; q < CH; q++) {
-                if (active && q0 + q < mine) ld8(Xm + (size_t)(par + 2 * (q0 + q)) * fs + n, x[q]);
+                if (active && q0 + q < mine) load8(Xm + (size_t)(par + 2 * (q0 + q)) * fs + n, x[q]);
                 else
 #pragma unroll
                     for (int k = 0; k < 8; k++) x[q][k] = 0.f;
@@ -159,17 +153,16 @@ __global__ void __launch_bounds__(kAdThreads, MINB) k_lap_ad(Geom g, Links32 U, 
                 if (active && fi < mine) {
                     const size_t off = (size_t)f * fs + (size_t)s * 32 + pmu * 8;
                     float xo[8], y[8];
-                    ld8(X + off, xo);
+                    load8(X + off, xo);
 #pragma unroll
                     for (int r = 0; r < 8; r++) y[r] = fmaf(b, acc[q][r], a * xo[r]);
                     if (HAS_W) {
                         float w[8];
-                        ld8(W + off, w);
+                        load8(W + off, w);
 #pragma unroll
                         for (int r = 0; r < 8; r++) y[r] = fmaf(c, w[r], y[r]);
                     }
-                    if (V8) store8_v8(Y + off, y);
-                    else store8(Y + off, y);
+                    store8(Y + off, y);
                     if (DOTS) {
 #pragma unroll
                         for (int r = 0; r < 8; r++) { yy = fmaf(y[r], y[r], yy); yx = fmaf(y[r], xo[r], yx); }
@@ -210,11 +203,11 @@ __global__ void __launch_bounds__(kAdThreads, MINB) k_lap_ad(Geom g, Links32 U, 
 struct AdShape { int ch, minb; };
 constexpr AdShape kAdShapes[2] = {{2, 3}, {3, 2}};
 
-template <int LF, bool HAS_W, bool DOTS, int CH, int MINB, bool V8>
+template <int LF, bool HAS_W, bool DOTS, int CH, int MINB>
 static int launch_ad_t(rmhmc_ctx* ctx, const float* X, float* Y, int nf, double a, double b, const float* W, double c,
                        int slot, cudaStream_t st) {
     if (DOTS && nf > kRedSlots) return set_err(ctx, RMHMC_EINVAL, "too many reduced fields");
-    auto kern = k_lap_ad<LF, HAS_W, DOTS, CH, MINB, V8>;
+    auto kern = k_lap_ad<LF, HAS_W, DOTS, CH, MINB>;
     const size_t smem = ad_smem_bytes(DOTS ? nf : 0);
     // the dynamic shared-memory limit of this instantiation, raised once per device to the largest size any
     // launch can ask for (kRedSlots reduced fields)
@@ -241,24 +234,15 @@ static int launch_ad_t(rmhmc_ctx* ctx, const float* X, float* Y, int nf, double 
     return RMHMC_OK;
 }
 
-template <int LF, int CH, int MINB, bool V8>
-static int launch_ad_w(rmhmc_ctx* ctx, const float* X, float* Y, int nf, double a, double b, const float* W, double c,
-                       int slot, cudaStream_t st) {
-    if (W) {
-        if (slot >= 0) return launch_ad_t<LF, true, true, CH, MINB, V8>(ctx, X, Y, nf, a, b, W, c, slot, st);
-        return launch_ad_t<LF, true, false, CH, MINB, V8>(ctx, X, Y, nf, a, b, W, c, slot, st);
-    }
-    if (slot >= 0) return launch_ad_t<LF, false, true, CH, MINB, V8>(ctx, X, Y, nf, a, b, W, c, slot, st);
-    return launch_ad_t<LF, false, false, CH, MINB, V8>(ctx, X, Y, nf, a, b, W, c, slot, st);
-}
-
-// 256-bit accesses when every field array is 32-byte aligned (the context's own buffers always are)
 template <int LF, int CH, int MINB>
 static int launch_ad_shape(rmhmc_ctx* ctx, const float* X, float* Y, int nf, double a, double b, const float* W,
                            double c, int slot, cudaStream_t st) {
-    const bool v8 = (uintptr_t)X % 32 == 0 && (uintptr_t)Y % 32 == 0 && (uintptr_t)W % 32 == 0;
-    if (v8) return launch_ad_w<LF, CH, MINB, true>(ctx, X, Y, nf, a, b, W, c, slot, st);
-    return launch_ad_w<LF, CH, MINB, false>(ctx, X, Y, nf, a, b, W, c, slot, st);
+    if (W) {
+        if (slot >= 0) return launch_ad_t<LF, true, true, CH, MINB>(ctx, X, Y, nf, a, b, W, c, slot, st);
+        return launch_ad_t<LF, true, false, CH, MINB>(ctx, X, Y, nf, a, b, W, c, slot, st);
+    }
+    if (slot >= 0) return launch_ad_t<LF, false, true, CH, MINB>(ctx, X, Y, nf, a, b, W, c, slot, st);
+    return launch_ad_t<LF, false, false, CH, MINB>(ctx, X, Y, nf, a, b, W, c, slot, st);
 }
 
 template <int LF>

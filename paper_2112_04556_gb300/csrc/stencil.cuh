@@ -1,6 +1,7 @@
 // The adjoint covariant hop sum of Sec. 2, Eq. (3) for one site and one field component mu:
 //   acc = 2 * sum_nu [ U_nu(x) X_mu(x+nu) U_nu(x)^dag + U_nu(x-nu)^dag X_mu(x-nu) U_nu(x-nu) ]
-// (the factor 2 comes from the doubled Hermitian expansion of the coefficients).
+// (the factor 2 comes from the doubled Hermitian expansion of the coefficients).  Every term is traceless, so
+// the sum is accumulated without its (2,2) entry (acc_*_tl) and read with herm2_to_coef_tl.
 //
 // Thread layout of the stencil kernels: 4 / NMU consecutive lanes own one site, each lane NMU of its four
 // field components (NMU = 1: a warp covers 8 consecutive sites, its loads of X_mu at a neighbour are one
@@ -33,7 +34,7 @@ __device__ __forceinline__ void hop_sum(const Geom& g, const typename LinksOf<T>
             for (int m = 0; m < NMU; m++) {
                 T x[8];
                 src(fwd[nu], mu0 + m, x);
-                acc_uxud(acc[m], uf, coef_to_herm2(x));
+                acc_uxud_tl(acc[m], uf, coef_to_herm2(x));
             }
         }
         {
@@ -42,7 +43,7 @@ __device__ __forceinline__ void hop_sum(const Geom& g, const typename LinksOf<T>
             for (int m = 0; m < NMU; m++) {
                 T x[8];
                 src(bwd[nu], mu0 + m, x);
-                acc_udxu(acc[m], ub, coef_to_herm2(x));
+                acc_udxu_tl(acc[m], ub, coef_to_herm2(x));
             }
         }
     }
@@ -66,8 +67,8 @@ __device__ __forceinline__ void hop_sum_prefetch(const Geom& g, const typename L
     for (int nu = 0; nu < 4; nu++) {
         const mat3<T> uf = LinkLoad<T, LF>::load(U, s, nu);
         const mat3<T> ub = LinkLoad<T, LF>::load(U, bwd[nu], nu);
-        acc_uxud(acc, uf, coef_to_herm2(xf[nu]));
-        acc_udxu(acc, ub, coef_to_herm2(xb[nu]));
+        acc_uxud_tl(acc, uf, coef_to_herm2(xf[nu]));
+        acc_udxu_tl(acc, ub, coef_to_herm2(xb[nu]));
     }
 }
 

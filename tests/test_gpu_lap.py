@@ -190,7 +190,7 @@ def test_lap_adjoint_every_shape_and_slab(L):
     """The multi-field adjoint kernel with every fields-per-pass choice and slab depths that leave a thinner
     last z block (7 = 3 + 3 + 1, 6 = 4 + 2), a slab that is not a whole number of 32-site tiles (5 x 6 x 2 =
     60 sites) and one z block holding the whole lattice; 7 fields (the last pass ragged).  The fields are
-    also taken at an offset of 16 bytes, which the kernel reads with 128-bit instead of 256-bit accesses."""
+    also taken at an offset of 16 bytes within a larger buffer."""
     import paper_2112_04556_gb300 as rm
     torch = torch_cuda()
     U = inputs.random_links(L, eps=0.7, seed=21)
