@@ -234,10 +234,11 @@ def lap_bytes_per_site(prec_bytes, linkfmt, nf):
 
 def lap_fma_per_site(form, nf, linkfmt=18):
     """FP32 pipe operations (FMA, or a single add or multiply) per site: the 3x3 form does 8 hops x 4 components
-    x 144 FMA per field (+24 per hop to rebuild the third row of 12-real links); the adjoint form builds 8
-    adjoint matrices (~270 operations each, +24 for 12-real links) and does 64 FMA per component hop."""
+    x 108 FMA per field (traceless conjugations; +24 per hop to rebuild the third row of 12-real links); the
+    adjoint form builds 8 adjoint matrices (~270 operations each, +24 for 12-real links) and does 64 FMA per
+    component hop."""
     if form == "3x3":
-        return 4608 * nf + (8 * 24 if linkfmt == 12 else 0)
+        return 3456 * nf + (8 * 24 if linkfmt == 12 else 0)
     return 8 * (270 + (24 if linkfmt == 12 else 0)) + 8 * 4 * 64 * nf
 
 
@@ -481,7 +482,7 @@ def main():
     cg_bytes = CG_BYTES_PER_SITE * V
     cg_avg_ms = cnt["cg_ms"] / max(cnt["cg_count"], 1)
     achieved = cg_bytes / (cg_avg_ms * 1e-3) / 1e9 if cnt["cg_count"] else None
-    alu_fma = 5000.0 * V   # per site: 8 hops x 4 components x 144 FMA + the fused axpy and epilogue
+    alu_fma = 3600.0 * V   # per site: 8 hops x 4 components x 108 FMA + the fused axpy and epilogue
     m = re.search(r"cg fp32 -> nmu (\d+) block (\d+)", rm.tuning(lat))
     shape = (int(m.group(1)), int(m.group(2))) if m else None
     traffic = CG_TRAFFIC_32.get(shape) if DIMS == (32, 32, 32, 32) else None
