@@ -62,7 +62,7 @@ ACCEPT_NSTEPS = 64
 # one ncu capture per launch shape (dram__bytes_read.sum + dram__bytes_write.sum;
 # profiles/k_cg_A_fp32_32x32x32x32.md), keyed by the tuned shape (components per lane, threads per block); a
 # shape without a capture reports null
-CG_TRAFFIC_32 = {(1, 256): 919.2e6, (2, 256): 926.8e6, (1, 128): 917.5e6, (0, 128): 937.5e6, (0, 256): 937.6e6}
+CG_TRAFFIC_32 = {(1, 256): 880.3e6, (2, 256): 885.9e6, (1, 128): 877.0e6, (0, 128): 936.9e6, (0, 256): 936.9e6}
 # algorithmic bytes per site of the conjugate-gradient stencil k_cg_A<float,18> (float32, 18-real links):
 # read r_k (128 B) and q_{k-1} (128 B), write q_k (128 B), four links of 72 B
 CG_BYTES_PER_SITE = 3 * 128 + 4 * 72
