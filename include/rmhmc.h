@@ -198,7 +198,9 @@ int rmhmc_tuning(const rmhmc_ctx* ctx, char* buf, int len);
                                   block 128 (the default): four lanes per link, the block's own basis rows read
                                   from global memory once per chunk of 4; nmu 1, block 128: the same rows staged
                                   once in shared memory (runs of up to 20 vectors); nmu 2, block 256: eight lanes
-                                  per link splitting the rows of the 8x8 accumulator, chunks of 8 */
+                                  per link splitting the rows of the 8x8 accumulator, chunks of 8; nmu 3, block
+                                  128: as nmu 0 with the neighbour rows loaded whole by the four lanes of a site
+                                  and passed through shared memory */
 #define RMHMC_SHAPE_LINKUPDATE 3   /* the float64 link update exp(i eps V) U (prec RMHMC_FP64, linkfmt 18, block
                                       128): nmu 1 (the default) in float-float arithmetic (two float32 numbers per
                                       value, ~2^-48 relative; rotations with Tr Q^2 / 2 >= 0.24 in float64), nmu 0

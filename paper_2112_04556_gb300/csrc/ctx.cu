@@ -236,8 +236,9 @@ extern "C" int rmhmc_set_stencil_shape(rmhmc_ctx* ctx, int kernel, int prec, int
         return RMHMC_OK;
     }
     if (kernel == RMHMC_SHAPE_KFORCE) {
-        if (prec != RMHMC_FP32 || linkfmt != 18 || nmu < 0 || nmu > 2 || block != (nmu == 2 ? 256 : 128))
-            return set_err(ctx, RMHMC_EINVAL, "kinetic-force contraction: RMHMC_FP32, 18, nmu 0/1 with block 128 or 2 with 256");
+        if (prec != RMHMC_FP32 || linkfmt != 18 || nmu < 0 || nmu > 3 || block != (nmu == 2 ? 256 : 128))
+            return set_err(ctx, RMHMC_EINVAL,
+                           "kinetic-force contraction: RMHMC_FP32, 18, nmu 0/1/3 with block 128 or 2 with 256");
         ctx->lg_mode = nmu;
         return RMHMC_OK;
     }

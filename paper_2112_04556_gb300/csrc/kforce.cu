@@ -486,6 +486,120 @@ __global__ void __launch_bounds__(kLsSites * 8, 2) k_link_grad_split(Geom g, Lin
     }
 }
 
+// The contraction of k_link_grad_krylov with the neighbour rows staged: in the C phase, lane (y, nu) needs
+// the whole row r_k(y + nu) (128 bytes); read lane by lane, one load instruction of a warp touches 32
+// different rows (one 32-byte sector each).  Here the 4 lanes of a site instead load the 4 chunks of each of
+// its 4 neighbour rows (one instruction: 8 whole rows), store them to shared memory (rows padded to 36
+// floats: a warp's 128-bit accesses fall on distinct bank quads), and after a barrier every lane reads its own
+// row there.
+constexpr int kNbRow = 36;
+template <int LF>
+__global__ void __launch_bounds__(kLgSites * 4, 4) k_link_grad_nbs(Geom g, Links32 U, const float* __restrict__ R,
+                                                                size_t fs, const int* __restrict__ flags, int n,
+                                                                const double* __restrict__ S, int ld,
+                                                                double* __restrict__ G) {
+    __shared__ __align__(16) float Ws[kLgSites * kLgPad];
+    __shared__ float Ss[kLgKC * kBasisCap];
+    __shared__ __align__(16) float Nb[4 * kLgSites * kNbRow];   // [nu][site][kNbRow]
+    if (flags) n = flags[1];
+    const int sl = threadIdx.x >> 2, q = threadIdx.x & 3;
+    float* const wrow = Ws + sl * kLgPad;
+    for (int base = blockIdx.x * kLgSites; base < g.V; base += gridDim.x * kLgSites) {
+        const int y = base + sl;
+        const bool live = y < g.V;
+        int fwd[4] = {0, 0, 0, 0}, bwd[4];
+        if (live) neighbours(g, y, fwd, bwd);
+        float C[8][8];
+#pragma unroll
+        for (int b = 0; b < 8; b++)
+#pragma unroll
+            for (int d = 0; d < 8; d++) C[b][d] = 0.f;
+        // chunk q of the 4 neighbour rows of basis vector k: registers, then shared memory
+        float t[4][8];
+        auto gload = [&](int k) {
+            const float* rk = R + (size_t)k * fs + q * 8;
+#pragma unroll
+            for (int nu = 0; nu < 4; nu++) load8_v8(rk + (size_t)fwd[nu] * 32, t[nu]);
+        };
+        auto sstore = [&]() {
+#pragma unroll
+            for (int nu = 0; nu < 4; nu++) {
+                float4* d = reinterpret_cast<float4*>(Nb + (nu * kLgSites + sl) * kNbRow + q * 8);
+                d[0] = make_float4(t[nu][0], t[nu][1], t[nu][2], t[nu][3]);
+                d[1] = make_float4(t[nu][4], t[nu][5], t[nu][6], t[nu][7]);
+            }
+        };
+        const float* const nrow = Nb + (q * kLgSites + sl) * kNbRow;
+        for (int k0 = 0; k0 < n; k0 += kLgKC) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < kLgKC * n; i += blockDim.x) {
+                const int kk = i / n, l = i - kk * n;
+                Ss[kk * kBasisCap + l] = k0 + kk < n ? (float)S[(size_t)(k0 + kk) * ld + l] : 0.f;
+            }
+            __syncthreads();
+            float w[kLgKC][8];
+#pragma unroll
+            for (int kk = 0; kk < kLgKC; kk++)
+#pragma unroll
+                for (int a = 0; a < 8; a++) w[kk][a] = 0.f;
+            if (live) {
+                for (int l = 0; l < n; l++) {
+                    float r[8];
+                    load8_v8(R + (size_t)l * fs + (size_t)y * 32 + q * 8, r);
+#pragma unroll
+                    for (int kk = 0; kk < kLgKC; kk++) {
+                        const float sv = Ss[kk * kBasisCap + l];
+#pragma unroll
+                        for (int a = 0; a < 8; a++) w[kk][a] = fmaf(sv, r[a], w[kk][a]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < kLgKC; kk++) store8(wrow + kk * 32 + q * 8, w[kk]);
+            const int kc = min(kLgKC, n - k0);   // uniform over the block
+            for (int kk = 0; kk < kc; kk++) {
+                if (live) {
+                    gload(k0 + kk);
+                    sstore();
+                }
+                __syncthreads();   // the rows of k (and, for kk = 0, the chunk's W) are in place
+                if (live) {
+#pragma unroll
+                    for (int mu = 0; mu < 4; mu++) {
+                        float rp[8], wv[8];
+                        lds8(nrow + mu * 8, rp);
+                        lds8(wrow + kk * 32 + mu * 8, wv);
+#pragma unroll
+                        for (int b = 0; b < 8; b++)
+#pragma unroll
+                            for (int d = 0; d < 8; d++) C[b][d] = fmaf(rp[b], wv[d], C[b][d]);
+                    }
+                }
+                __syncthreads();   // every lane has read the rows of k
+            }
+        }
+        if (live) {
+            const mat3<float> u = LinkLoad<float, LF>::load(U, y, q);
+            float Gk[8];
+#pragma unroll
+            for (int a = 0; a < 8; a++) Gk[a] = 0.f;
+#pragma unroll
+            for (int d = 0; d < 8; d++) {
+                float col[8], rc[8];
+#pragma unroll
+                for (int b = 0; b < 8; b++) col[b] = C[b][d];
+                herm<float> E = h_zero<float>();
+                acc_uxud_tl(E, u, coef_to_herm2(col));   // 2 sum_c (R C)_cd T^c
+                herm2_to_coef_tl(E, rc);                  // (R C)_cd
+                f_contract(d, rc, Gk);
+            }
+            double* out = G + (size_t)y * 32 + q * 8;
+#pragma unroll
+            for (int a = 0; a < 8; a++) out[a] = (double)Gk[a] * (1.0 / 16.0);
+        }
+    }
+}
+
 // F_K from the basis rows (X_j rows 0..ns-1, Z_j rows ns..2ns-1, row stride ldr, device float64) of the
 // float32 basis R; n on the host, or read on the device from flags[1] when flags is given
 int link_grad_krylov_launch(rmhmc_ctx* ctx, const float* R, const double* rows, int ldr, int ns, const double* alpha,
@@ -498,7 +612,11 @@ int link_grad_krylov_launch(rmhmc_ctx* ctx, const float* R, const double* rows, 
     for (int j = 0; j < ns; j++) pw.w[j] = alpha[j];
     k_pair_matrix<<<ctx->num_sms / 4 > 1 ? ctx->num_sms / 4 : 1, 256, 0, st>>>(rows, ldr, ns, pw, flags, n, S, kBasisCap);
     ++ctx->launches;
-    if (ctx->lg_mode == 2) {
+    if (ctx->lg_mode == 3) {
+        const int grid = capped_grid(ctx, (size_t)ctx->g.V * 4, kLgSites * 4);
+        k_link_grad_nbs<18><<<grid, kLgSites * 4, 0, st>>>(ctx->g, links32(ctx), R, field_elems(ctx), flags, n, S,
+                                                           kBasisCap, F);
+    } else if (ctx->lg_mode == 2) {
         const int ntile = (ctx->g.V + kLsSites - 1) / kLsSites;
         const int grid = std::max(1, std::min(ntile, (int)ctx->num_sms * 2));
         k_link_grad_split<18><<<grid, kLsSites * 8, 0, st>>>(ctx->g, links32(ctx), R, field_elems(ctx), flags, n, S,

@@ -133,12 +133,13 @@ def test_autograd_laplacian():
     assert rel_l2(host(omega.grad), oracle.lap_link_grad(L, U, X, G, [1.0])) <= 1e-12
 
 
-@pytest.mark.parametrize("L", [(8, 6, 4, 10), (16, 16, 16, 16)])
+@pytest.mark.parametrize("L", [(8, 6, 4, 10), (5, 3, 4, 7), (16, 16, 16, 16)])
 def test_staged_contraction_matches_global(L):
-    """The three kernels of the kinetic force's basis contraction (four lanes per link reading the own basis rows
-    from global memory, the same with the rows staged in shared memory, eight lanes per link splitting the
-    accumulator) agree to float32 rounding and match the oracle's force; a tight tolerance makes the Krylov run
-    longer than the 20 staged rows, which takes the global reads inside the staged kernel."""
+    """The four kernels of the kinetic force's basis contraction (four lanes per link reading the own basis rows
+    from global memory; the same with the rows staged in shared memory; eight lanes per link splitting the
+    accumulator; four lanes with the neighbour rows passed through shared memory) agree to float32 rounding
+    and match the oracle's force; a tight tolerance makes the Krylov run longer than the 20 staged rows, which
+    takes the global reads inside the staged kernel.  5 x 3 x 4 x 7 = 420 sites leaves a ragged last block."""
     import paper_2112_04556_gb300 as rm
     U = inputs.random_links(L, eps=0.4, seed=41)
     P = inputs.gaussian_fields(L, 1, seed=42)[0]
@@ -146,17 +147,18 @@ def test_staged_contraction_matches_global(L):
     out = {}
     with rm.Context(L) as ctx:
         Ud, Pd = dev(U), dev(P)
-        for mode, block in ((1, 128), (0, 128), (2, 256)):
+        for mode, block in ((1, 128), (0, 128), (2, 256), (3, 128)):
             rm.set_stencil_shape(ctx, rm.SHAPE_KFORCE, rm.FP32, 18, mode, block)
             for tol in (1e-6, 1e-9):
                 out[(mode, tol)] = host(rm.kinetic_force(ctx, Ud, Pd, m, tol=tol, prec=rm.MIXED)[0])
-        for bad in ((2, 128), (3, 256), (0, 256)):
+        for bad in ((2, 128), (3, 256), (0, 256), (4, 128)):
             with pytest.raises(rm.RmhmcError):
                 rm.set_stencil_shape(ctx, rm.SHAPE_KFORCE, rm.FP32, 18, *bad)
     for tol in (1e-6, 1e-9):
         assert rel_l2(out[(1, tol)], out[(0, tol)]) <= 1e-6, tol
         assert rel_l2(out[(2, tol)], out[(0, tol)]) <= 1e-6, tol
+        assert rel_l2(out[(3, tol)], out[(0, tol)]) <= 1e-6, tol
     if np.prod(L) <= 4096:
         _, ref, _ = oracle.kinetic(L, U, P, m, tol=1e-13)
-        for mode in (0, 1, 2):
+        for mode in (0, 1, 2, 3):
             assert rel_l2(out[(mode, 1e-9)], ref) <= 1e-5
