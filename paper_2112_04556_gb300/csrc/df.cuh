@@ -14,11 +14,6 @@ struct dfl { float hi, lo; };
 struct cdfl { dfl re, im; };
 
 __device__ __forceinline__ dfl df_make(float h, float l) { dfl r; r.hi = h; r.lo = l; return r; }
-__device__ __forceinline__ dfl df_from(double x) {
-    const float h = __double2float_rn(x);
-    return df_make(h, __double2float_rn(x - (double)h));
-}
-__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
 // s + e = a + b exactly (TwoSum)
 __device__ __forceinline__ dfl two_sum(float a, float b) {
     const float s = __fadd_rn(a, b);
@@ -31,11 +26,11 @@ __device__ __forceinline__ dfl quick_two_sum(float a, float b) {
     const float s = __fadd_rn(a, b);
     return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
-// The same conversions from the IEEE-754 bit fields, with integer operations and no float64 arithmetic (float64
-// runs at a small fraction of the float32 rate on this part).  df_split: hi = x rounded to 24 significant bits
-// (its 29 low significand bits dropped, rounding half away from zero, a carry moving into the exponent), lo =
-// the signed remainder (at most 2^28 units of x's last place) as a float times 2^(e - 52); |lo| <= ulp(hi) / 2
-// and hi + lo = x to 2^-49 |x|, as for the float64 rounding of df_from.  |x| below 2^-126 gives 0 and |x|
+// Conversions between float64 and float pairs from the IEEE-754 bit fields, with integer operations and no
+// float64 arithmetic (float64 runs at a small fraction of the float32 rate on this part).  df_split: hi = x
+// rounded to 24 significant bits (its 29 low significand bits dropped, rounding half away from zero, a carry
+// moving into the exponent), lo = the signed remainder (at most 2^28 units of x's last place) as a float times
+// 2^(e - 52); |lo| <= ulp(hi) / 2 and hi + lo = x to 2^-49 |x|.  |x| below 2^-126 gives 0 and |x|
 // near or above 2^128 gives +-inf (NaN too); lo is dropped for |x| < 2^-74 (an absolute error below 2^-98).
 __device__ __forceinline__ dfl df_split(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);

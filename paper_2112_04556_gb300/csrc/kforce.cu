@@ -490,8 +490,8 @@ __global__ void __launch_bounds__(kLsSites * 8, 2) k_link_grad_split(Geom g, Lin
 // the whole row r_k(y + nu) (128 bytes); read lane by lane, one load instruction of a warp touches 32
 // different rows (one 32-byte sector each).  Here the 4 lanes of a site instead load the 4 chunks of each of
 // its 4 neighbour rows (one instruction: 8 whole rows), store them to shared memory (rows padded to 36
-// floats: a warp's 128-bit accesses fall on distinct bank quads), and after a barrier every lane reads its own
-// row there.
+// floats: a warp's 128-bit accesses fall on distinct bank quads), and after a warp barrier (the four lanes of a
+// site are in one warp) every lane reads its own row there.
 constexpr int kNbRow = 36;
 template <int LF>
 __global__ void __launch_bounds__(kLgSites * 4, 4) k_link_grad_nbs(Geom g, Links32 U, const float* __restrict__ R,
@@ -562,7 +562,8 @@ __global__ void __launch_bounds__(kLgSites * 4, 4) k_link_grad_nbs(Geom g, Links
                     gload(k0 + kk);
                     sstore();
                 }
-                __syncthreads();   // the rows of k (and, for kk = 0, the chunk's W) are in place
+                __syncwarp();   // the rows of k (and, for kk = 0, the chunk's W) are in place: a site's
+                                // rows and W are written and read by its own four lanes, within one warp
                 if (live) {
 #pragma unroll
                     for (int mu = 0; mu < 4; mu++) {
@@ -575,7 +576,7 @@ __global__ void __launch_bounds__(kLgSites * 4, 4) k_link_grad_nbs(Geom g, Links
                             for (int d = 0; d < 8; d++) C[b][d] = fmaf(rp[b], wv[d], C[b][d]);
                     }
                 }
-                __syncthreads();   // every lane has read the rows of k
+                __syncwarp();   // the site's lanes have read the rows of k
             }
         }
         if (live) {
