@@ -221,8 +221,8 @@ def run_reference(args, rank, world):
 
 def md_solves_estimate(nsteps):
     """Kinetic evaluations of one trajectory at the headline settings: 4 fixed-point iterations to the tolerance
-    plus MIXED_FP_EXTRA, for each of the two fixed points of every step, and the first force (the GPU runs count
-    these; at 20 steps 141 + 140)."""
+    plus MIXED_FP_EXTRA, for each of the two fixed points of every step (each iterate of either needs a Krylov
+    run: a kinetic force or a velocity), and the first force (the GPU runs count these; at 20 steps 161 + 160)."""
     return 2 * nsteps * (4 + MIXED_FP_EXTRA) + 1
 
 
